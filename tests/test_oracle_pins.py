@@ -1,0 +1,432 @@
+"""Pins of the FP64 reference step to facts fixed by the paper and by the
+mathematics (not by re-typing its formulas).  CPU only.
+
+Each test names what it pins and which mistake it would catch.
+"""
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import lbm_oracle as o
+from oracle import theory as th
+from paper_1905_09554_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def load_table(name):
+    return np.loadtxt(os.path.join(GOLDEN, name), comments="#")
+
+
+# ---------------------------------------------------------------- lattice
+def test_d3q19_moment_isotropy():
+    """Weights and velocities: isotropy up to 4th order (textbook D3Q19).
+    A wrong weight or a missing/duplicated velocity breaks one of these."""
+    c, w = o.C.astype(float), o.W
+    assert c.shape == (19, 3)
+    assert len({tuple(v) for v in o.C}) == 19
+    assert {tuple(-v) for v in o.C} == {tuple(v) for v in o.C}
+    d = np.eye(3)
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert np.abs(np.einsum("a,ai->i", w, c)).max() < 1e-16
+    assert np.allclose(np.einsum("a,ai,aj->ij", w, c, c), d / 3.0, atol=1e-16)
+    assert np.abs(np.einsum("a,ai,aj,ak->ijk", w, c, c, c)).max() < 1e-16
+    fourth = np.einsum("a,ai,aj,ak,al->ijkl", w, c, c, c, c)
+    iso = (np.einsum("ij,kl->ijkl", d, d) + np.einsum("ik,jl->ijkl", d, d)
+           + np.einsum("il,jk->ijkl", d, d)) / 9.0
+    assert np.allclose(fourth, iso, atol=1e-16)
+
+
+# ------------------------------------------------------------ equilibrium
+def test_equilibrium_moments_closed_form():
+    """Eq. local_eq (with the leading 1 restored): sum f_eq = rho,
+    sum c f_eq = rho u, sum c c f_eq = rho cs2 I + rho u u."""
+    rng = np.random.default_rng(1)
+    rho = rng.uniform(0.05, 2.5, size=(3, 4, 5))
+    u = rng.uniform(-0.1, 0.1, size=(3, 3, 4, 5))
+    feq = o.equilibrium(rho, u)
+    c = o.C.astype(float)
+    assert np.abs(feq.sum(0) - rho).max() < 1e-14
+    assert np.abs(np.einsum("ai,a...->i...", c, feq) - rho * u).max() < 1e-15
+    pi = np.einsum("ai,aj,a...->ij...", c, c, feq)
+    want = (np.eye(3)[:, :, None, None, None] * rho / 3.0
+            + rho * u[:, None] * u[None, :])
+    assert np.abs(pi - want).max() < 1e-14
+
+
+# ----------------------------------------------------------------- force
+def _rho_for_psi(psi):
+    """Density whose pseudo-potential (rho0 = 1) equals psi."""
+    return -np.log(1.0 - psi)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_force_of_sinusoidal_psi_along_an_axis(axis):
+    """For psi = a + b sin(k s) along one axis, the single-belt force is
+    F_s = -G psi b cos(k s) sin(k) * (sum of w over c_s = +1, times 2) =
+    -G psi b cos(k s) sin(k) / 3; the other components vanish.  Catches a
+    wrong neighbour direction, weight or sign in Eq. SC_force."""
+    n = [6, 7, 8]
+    L = n[axis]
+    k = 2 * math.pi / L
+    a, b, G = 0.55, 0.2, -5.5
+    shape = (n[2], n[1], n[0])
+    idx = np.indices(shape)[2 - axis].astype(float)
+    psi = a + b * np.sin(k * idx)
+    F = o.shan_chen_force(_rho_for_psi(psi), G)
+    want = -G * psi * b * np.cos(k * idx) * math.sin(k) / 3.0
+    for i in range(3):
+        if i == axis:
+            assert np.abs(F[i] - want).max() < 1e-14
+        else:
+            assert np.abs(F[i]).max() < 1e-15
+
+
+def test_force_of_diagonal_sinusoidal_psi():
+    """psi = a + b sin(k (x + y)) exercises the edge velocities:
+    F_x = F_y = -G psi b cos(k(x+y)) [(2/9) sin k + (1/18) sin 2k], F_z = 0."""
+    L = 8
+    k = 2 * math.pi / L
+    a, b, G = 0.5, 0.25, -5.3
+    z, y, x = np.indices((3, L, L)).astype(float)
+    th_ = k * (x + y)
+    psi = a + b * np.sin(th_)
+    F = o.shan_chen_force(_rho_for_psi(psi), G)
+    fac = (2.0 / 9.0) * math.sin(k) + (1.0 / 18.0) * math.sin(2 * k)
+    want = -G * psi * b * np.cos(th_) * fac
+    assert np.abs(F[0] - want).max() < 1e-14
+    assert np.abs(F[1] - want).max() < 1e-14
+    assert np.abs(F[2]).max() < 1e-15
+
+
+def test_force_sums_to_zero_on_periodic_box():
+    """Sum over a periodic box of F vanishes (pairs c, -c cancel), and F = 0
+    for a uniform field."""
+    rho = inputs.random_density(5, 6, 7, seed=3)
+    F = o.shan_chen_force(rho, -5.5)
+    assert np.abs(F.sum(axis=(1, 2, 3))).max() <= 1e-13 * np.abs(F).sum()
+    Fu = o.shan_chen_force(np.full((4, 4, 4), 1.3), -5.5)
+    assert np.abs(Fu).max() < 1e-15
+
+
+# -------------------------------------------------------------- streaming
+def test_streaming_moves_each_population_by_its_velocity():
+    """Eq. LBE: f_a(x + c_a, t + 1) = f*_a(x, t), with periodic wrap."""
+    shape = (5, 4, 3)
+    for a in range(19):
+        fs = np.zeros((19,) + shape)
+        x0, y0, z0 = 2, 3, 4  # at the high edge in y and z: wraps for +c
+        fs[a, z0, y0, x0] = 1.0
+        out = o.stream(fs)
+        cx, cy, cz = o.C[a]
+        want = np.zeros((19,) + shape)
+        want[a, (z0 + cz) % 5, (y0 + cy) % 4, (x0 + cx) % 3] = 1.0
+        assert np.array_equal(out, want), a
+
+
+# -------------------------------------------------------------- collision
+@pytest.mark.parametrize("coll", ["srt", "mrt", "mrt-random"])
+def test_collision_conserves_mass_and_adds_the_force(coll):
+    """Both operators conserve rho; the momentum after collision is j + F
+    exactly (shift: rho (u' - u)/tau = F; Guo: by construction)."""
+    rng = np.random.default_rng(7)
+    shape = (3, 4, 5)
+    rho = rng.uniform(0.1, 2.4, size=shape)
+    u = rng.uniform(-0.05, 0.05, size=(3,) + shape)
+    f = o.equilibrium(rho, u) * (1 + 0.05 * rng.standard_normal((19,) + shape))
+    F = rng.uniform(-0.1, 0.1, size=(3,) + shape)
+    tau = 0.7
+    if coll == "srt":
+        fs = o.collide_srt(f, F, tau)
+    else:
+        s = o.mrt_rates(tau) if coll == "mrt" else rng.uniform(0.5, 1.9, 19)
+        fs = o.collide_mrt(f, F, s)
+    assert np.abs(fs.sum(0) - f.sum(0)).max() < 1e-14
+    dj = o.momentum(fs) - o.momentum(f)
+    assert np.abs(dj - F).max() < 1e-14
+
+
+def test_mrt_basis_is_orthogonal_and_holds_the_conserved_moments():
+    """d'Humieres D3Q19 basis: rows mutually orthogonal, row 0 = density,
+    rows 3, 5, 7 = momentum components; M^-1 M = I."""
+    M = o.M
+    G = M @ M.T
+    assert np.abs(G - np.diag(np.diag(G))).max() == 0.0
+    assert (np.diag(G) > 0).all()
+    assert np.abs(o.M_INV @ M - np.eye(19)).max() < 1e-14
+    assert np.array_equal(M[0], np.ones(19))
+    for row, i in ((3, 0), (5, 1), (7, 2)):
+        assert np.array_equal(M[row], o.C[:, i].astype(float))
+
+
+def test_mrt_with_equal_rates_is_bgk_with_guo_forcing():
+    """With every rate 1/tau, M^-1 Lambda M = I/tau and the MRT step equals
+    the population-space BGK-Guo step
+    f* = f - (f - f_eq(u_b))/tau + (1 - 1/(2 tau)) S.  Catches a transposed
+    basis, a wrong inverse or a misplaced (I - Lambda/2)."""
+    rng = np.random.default_rng(11)
+    shape = (2, 3, 4)
+    rho = rng.uniform(0.1, 2.4, size=shape)
+    u = rng.uniform(-0.05, 0.05, size=(3,) + shape)
+    f = o.equilibrium(rho, u) * (1 + 0.05 * rng.standard_normal((19,) + shape))
+    F = rng.uniform(-0.1, 0.1, size=(3,) + shape)
+    for tau in (0.6, 1.0, 1.7):
+        fs = o.collide_mrt(f, F, np.full(19, 1.0 / tau))
+        r = f.sum(0)
+        ub = (o.momentum(f) + 0.5 * F) / r
+        want = f - (f - o.equilibrium(r, ub)) / tau + (1 - 0.5 / tau) * o.guo_source(ub, F)
+        assert np.abs(fs - want).max() < 1e-14
+
+
+def test_mrt_rate_rules():
+    """Sec. 2: s2 = s10 = s12 = s14 = s15 = s16 = omega (1-based), others 1,
+    with omega = 1/tau; at tau = 1 every rate is 1."""
+    s = o.mrt_rates(0.8)
+    assert np.allclose(s[[1, 9, 11, 13, 14, 15]], 1.25)
+    others = [k for k in range(19) if k not in (1, 9, 11, 13, 14, 15)]
+    assert np.allclose(s[others], 1.0)
+    assert np.allclose(o.mrt_rates(1.0), 1.0)
+    sh = o.mrt_rates(0.8, rule="shear")
+    assert sh[1] == 1.0 and np.allclose(sh[[9, 11, 13, 14, 15]], 1.25)
+
+
+# ------------------------------------------------------------ fixed points
+@pytest.mark.parametrize("coll", ["srt", "mrt"])
+def test_uniform_states_are_fixed_points(coll):
+    """Uniform rho (F = 0) at rest or moving with u0 is an exact equilibrium."""
+    p = o.Params(G=-5.5, tau=0.8, collision=coll)
+    rho = np.full((4, 5, 6), 0.9)
+    for u0 in ((0, 0, 0), (0.03, -0.02, 0.01)):
+        u = np.zeros((3,) + rho.shape) + np.array(u0)[:, None, None, None]
+        f0 = o.init_populations(rho, u)
+        f = o.run(f0, 5, p)
+        assert np.abs(f - f0).max() < 1e-15
+
+
+@pytest.mark.parametrize("coll", ["srt", "mrt"])
+def test_global_mass_and_momentum_conserved_over_a_ligament_run(coll):
+    """Total mass and total momentum are conserved exactly (sum F = 0) over
+    a perturbed noisy ligament run (1e-13 relative)."""
+    rl, rv = inputs.COEXISTENCE[("shift" if coll == "srt" else "guo", -5.5, 1.0)]
+    rho = inputs.noisy_ligament_density(12, 12, 24, 3.5, 0.1, rl, rv, 1e-3, seed=5)
+    s = o.mrt_rates(0.8, rule="shear") if coll == "mrt" else None
+    p = o.Params(G=-5.5, tau=0.8, collision=coll, s=s)
+    f = o.init_populations(rho)
+    m0 = f.sum()
+    j0 = o.momentum(f).sum(axis=(1, 2, 3))
+    f = o.run(f, 300, p)
+    assert abs(f.sum() - m0) <= 1e-13 * m0
+    assert np.abs(o.momentum(f).sum(axis=(1, 2, 3)) - j0).max() <= 1e-13 * m0
+    assert np.isfinite(f).all()
+
+
+# --------------------------------------------------------------- viscosity
+@pytest.mark.parametrize("coll,tau", [("srt", 0.8), ("srt", 1.3), ("mrt", 0.6), ("mrt", 0.8)])
+def test_shear_wave_decays_with_the_lattice_viscosity(coll, tau):
+    """A small shear wave in a uniform stable liquid decays as
+    exp(-nu k^2 t), nu = cs2 (tau - 1/2) (the MRT shear rate sets the same
+    nu).  64-cell wavelength; the lattice correction is O(k^2) ~ 1e-3."""
+    L = 64
+    k = 2 * math.pi / L
+    y = np.arange(L)
+    rho = np.full((1, L, 1), 2.3)
+    u = np.zeros((3, 1, L, 1))
+    u[0, 0, :, 0] = 1e-4 * np.sin(k * y)
+    p = o.Params(G=-5.5, tau=tau, collision=coll)
+    f = o.init_populations(rho, u)
+    amps = []
+    for t in range(400):
+        _, ub = o.macroscopic(f, p)
+        amps.append(2.0 / L * (ub[0, 0, :, 0] * np.sin(k * y)).sum())
+        f = o.step(f, p)
+    slope = np.polyfit(np.arange(100, 400), np.log(amps[100:]), 1)[0]
+    nu = (tau - 0.5) / 3.0
+    assert abs(-slope / (k * k) / nu - 1.0) < 2e-3
+
+
+# -------------------------------------------------------- flat interfaces
+def flat_interface(G, coll, tau, rl, rv, n=32, max_steps=40000, s=None):
+    """Run a flat liquid slab (fields vary along z only) to steady state;
+    return (rho_liquid_centre, rho_vapour_centre, final f)."""
+    z = np.arange(n) + 0.5
+    d = np.abs(z - n / 2) - n / 4
+    rho = (rv + 0.5 * (rl - rv) * (1 - np.tanh(d / 2.0)))[:, None, None]
+    if s is None and coll == "mrt":
+        s = o.mrt_rates(tau)
+    p = o.Params(G=G, tau=tau, collision=coll, s=s)
+    f = o.init_populations(rho)
+    prev = None
+    for k in range(0, max_steps, 500):
+        f = o.run(f, 500, p)
+        r = f.sum(0)[:, 0, 0]
+        cur = (r[n // 2], r[0])
+        if prev is not None and max(abs(cur[0] - prev[0]), abs(cur[1] - prev[1])) < 1e-12:
+            break
+        prev = cur
+    else:
+        raise AssertionError("flat interface did not reach steady state")
+    return cur[0], cur[1], f
+
+
+@pytest.mark.slow
+def test_flat_interface_guo_tau1_satisfies_the_discrete_balance():
+    """At tau = 1 with Guo forcing, a steady flat interface has u_b = 0, so
+    f* = w (rho + 3 c.F / 2) and one streaming step must return it.  Summing
+    the 0th and 1st moments over the lumped 1-D lattice (weight 1/6 per
+    direction) gives two exact difference equations:
+      (rho+ - 2 rho + rho-)/6 = (F+ - F-)/4,
+      (rho+ - rho-)/6 = (F+ + 2F + F-)/4,
+    with F(z) = -G psi(z) (psi(z+1) - psi(z-1))/6."""
+    G = -5.3
+    _, _, f = flat_interface(G, "mrt", 1.0, 2.1086, 0.0778)
+    r = f.sum(0)[:, 0, 0]
+    ps = 1 - np.exp(-r)
+    F = -G * ps * (np.roll(ps, -1) - np.roll(ps, 1)) / 6.0
+    rp, rm, Fp, Fm = np.roll(r, -1), np.roll(r, 1), np.roll(F, -1), np.roll(F, 1)
+    assert np.abs((rp - 2 * r + rm) / 6 - (Fp - Fm) / 4).max() < 1e-9
+    assert np.abs((rp - rm) / 6 - (Fp + 2 * F + Fm) / 4).max() < 1e-9
+
+
+@pytest.mark.slow
+def test_flat_interface_matches_table_2_and_is_tau_independent_for_mrt():
+    """Table 2 (MRT, G0 = -5.3): rho_l = 2.1086, rho_v = 0.0778 for every
+    tau in the table; the lattice steady state matches to 5e-4 and does not
+    depend on tau (1e-5), as Sec. 2 states for MRT."""
+    t2 = load_table("paper_table2_mrt.txt")
+    tau_a, rl_a, rv_a = t2[0][3], t2[0][5], t2[0][6]
+    tau_b = t2[-1][3]
+    la, va, _ = flat_interface(-5.3, "mrt", tau_a, rl_a, rv_a)
+    lb, vb, _ = flat_interface(-5.3, "mrt", tau_b, rl_a, rv_a)
+    assert abs(la - rl_a) < 5e-4 and abs(va - rv_a) < 5e-4
+    assert abs(la - lb) < 1e-5 and abs(va - vb) < 1e-5
+    il, iv = th.coexistence_integral(-5.3, 0.0)
+    assert abs(la - il) < 1.5e-3 and abs(va - iv) < 1.5e-3
+
+
+@pytest.mark.slow
+def test_flat_interface_srt_matches_table_1_and_depends_on_tau():
+    """Table 1 (SRT, G0 = -5.3): at tau = 0.67926 rho_l = 2.1167 and
+    rho_v = 0.0836 (match to 6e-4); coexistence densities rise with tau
+    (Table 1's trend, tau = 1.10647 -> 2.1775 / 0.1383)."""
+    t1 = load_table("paper_table1_srt.txt")
+    tau_a, rl_a, rv_a = t1[0][3], t1[0][5], t1[0][6]
+    tau_b, rl_b, rv_b = t1[-1][3], t1[-1][5], t1[-1][6]
+    la, va, _ = flat_interface(-5.3, "srt", tau_a, rl_a, rv_a)
+    lb, vb, _ = flat_interface(-5.3, "srt", tau_b, rl_b, rv_b)
+    assert abs(la - rl_a) < 6e-4 and abs(va - rv_a) < 6e-4
+    assert abs(lb - rl_b) < 2e-3 and abs(vb - rv_b) < 2e-3
+    assert (lb - la) > 0.5 * (rl_b - rl_a) and (vb - va) > 0.5 * (rv_b - rv_a)
+
+
+@pytest.mark.slow
+def test_flat_interface_srt_tau1_matches_the_shift_integral():
+    """Velocity-shift forcing at tau = 1 follows the psi'/psi^2 mechanical
+    stability integral (G = -5.5) to 1.5e-3."""
+    rl, rv, _ = flat_interface(-5.5, "srt", 1.0, 2.3068, 0.1041)
+    il, iv = th.coexistence_integral(-5.5, 1.0, guess=(2.3, 0.1))
+    assert abs(rl - il) < 1.5e-3 and abs(rv - iv) < 1.5e-3
+
+
+# ------------------------------------------------------------------ Laplace
+@pytest.mark.slow
+def test_laplace_law_for_static_cylinders():
+    """Laplace test (Sec. 3): dp = P(rho_in) - P(rho_out) = sigma / R for
+    periodic cylinders at three radii (MRT-Guo, G0 = -5.3, tau = 1).  dp R is
+    constant to 5%, dp falls with R, and sigma at the largest radius is Table
+    2's 0.0495 within 2%."""
+    G = -5.3
+    t2 = load_table("paper_table2_mrt.txt")
+    sigma_paper = t2[:, 7].mean()
+    p = o.Params(G=G, tau=1.0, collision="mrt")
+    res = []
+    for R, L, steps in ((8, 40, 2000), (12, 56, 3000), (16, 72, 5000)):
+        yy = np.arange(L)[:, None] - (L - 1) / 2
+        xx = np.arange(L)[None, :] - (L - 1) / 2
+        r = np.sqrt(xx * xx + yy * yy)
+        rho = (0.0781 + 0.5 * (2.1089 - 0.0781) * (1 - np.tanh((r - R) / 2)))[None]
+        f = o.run(o.init_populations(rho), steps, p)
+        rho = f.sum(0)[0]
+        rin, rout = rho[L // 2, L // 2], rho[0, 0]
+        dp = o.pressure(rin, G) - o.pressure(rout, G)
+        Re = math.sqrt(((rho - rout) / (rin - rout)).sum() / math.pi)
+        res.append((Re, dp))
+    prods = [dp * Re for Re, dp in res]
+    assert res[0][1] > res[1][1] > res[2][1] > 0
+    assert max(prods) / min(prods) < 1.05
+    assert abs(prods[-1] / sigma_paper - 1) < 0.02
+
+
+# ----------------------------------------------------- theory-side pins
+def test_coexistence_integral_matches_table_2():
+    """The continuum (psi'/psi) integral at G0 = -5.3 reproduces Table 2's
+    MRT densities to 3e-4."""
+    rl, rv = th.coexistence_integral(-5.3, 0.0)
+    assert abs(rl - 2.1086) < 3e-4 and abs(rv - 0.0778) < 3e-4
+    assert abs(th.eos(rl, -5.3) - th.eos(rv, -5.3)) < 1e-12
+
+
+def test_linear_stability_curve_of_fig_3():
+    """Fig. 3's LSA curve is T = ln(1/eps)/omega with one omega; the viscous
+    cylinder relation at Oh = 0.1 and the figure's k R0 = 2 pi 98/896 gives
+    that omega to the paper's two significant figures (0.28)."""
+    d = load_table("paper_fig3_lsa.txt")
+    om = np.log(1.0 / d[:, 0]) / d[:, 1]
+    assert om.std() < 1e-8
+    x = 2 * math.pi * 98 / (1792 / 2)
+    w = th.viscous_cylinder(x, 0.1)
+    assert abs(w - om.mean()) < 0.005
+    assert abs(th.linear_breakup_time(0.05, om.mean()) - 10.699) < 1e-3
+
+
+def test_viscous_cylinder_limits():
+    """Oh -> 0 gives Rayleigh's inviscid rate; at long wavelength the full
+    relation approaches the slender-jet equation; x >= 1 is stable."""
+    for x in (0.3, 0.7, 0.9):
+        assert abs(th.viscous_cylinder(x, 1e-7) - th.rayleigh_inviscid(x)) < 1e-3
+    assert abs(th.viscous_cylinder(0.05, 0.1) / th.viscous_long_wave(0.05, 0.1) - 1) < 0.01
+    assert th.viscous_cylinder(1.2, 0.1) == 0.0
+
+
+# -------------------------------------------------------- input generators
+def test_splitmix64_reference_values():
+    """First two outputs of SplitMix64 from state 0 (published test vector)."""
+    z = inputs.splitmix64(np.arange(2, dtype=np.uint64), 0)
+    assert int(z[0]) == 0xE220A8397B1DCDAF
+    assert int(z[1]) == 0x6E789E6AA1B965F4
+
+
+def test_gaussian_generator_statistics():
+    g = inputs.gaussian(200000, seed=1)
+    assert abs(g.mean()) < 0.01 and abs(g.std() - 1) < 0.01
+    assert np.array_equal(g[:1000], inputs.gaussian(1000, seed=1))
+
+
+def test_ligament_profile_geometry():
+    rl, rv = 2.3, 0.1
+    rho = inputs.ligament_density(32, 32, 64, 8.0, 0.05, rl, rv)
+    assert rho.shape == (64, 32, 32)
+    assert rho.max() < rl and rho.min() > rv
+    # widest slice at z = 0 (cos = 1), narrowest at z = nz/2
+    a = (rho > 0.5 * (rl + rv)).sum(axis=(1, 2))
+    assert a[0] == a.max() and a[32] == a.min()
+
+
+def test_batch_instances_are_deterministic_and_uneven():
+    b = inputs.batch_instances(64, seed=0)
+    assert len(b) == 64 and b == inputs.batch_instances(64, seed=0)
+    assert {d["R0"] for d in b} <= {8.0, 12.0, 16.0}
+    assert all(0.2 <= d["kR0"] < 1.0 for d in b)
+    assert len({(d["nx"], d["nz"]) for d in b}) > 10
+
+
+def test_coexistence_constants_match_the_golden_file():
+    """The ligament inputs' end-point densities are the ones the committed
+    script wrote from the reference step."""
+    import json
+    with open(os.path.join(GOLDEN, "coexistence.json")) as fh:
+        cases = json.load(fh)["cases"]
+    for c in cases:
+        assert inputs.COEXISTENCE[(c["forcing"], c["G"], c["tau"])] == (c["rho_l"], c["rho_v"])
