@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Benchmark of the D3Q19 Shan-Chen lattice Boltzmann step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (default): the sharp-interface ligament R0 = 64, kR0 = 0.7 in a
+256 x 256 x 575 periodic box (37.7 M cells), G = -5.5, SRT with velocity shift
+at tau = 1, FP32 populations, 5% cosine perturbation.  A step is one fused
+step-kernel launch over the whole box; inputs (2 x 2.86 GB population copies)
+are far larger than L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  `value` is MLUPS (million lattice updates per
+second) over all ranks, device-timed with CUDA events; `e2e` is the same
+metric through the C ABI with host buffers (initial density uploaded from
+pinned host memory, diagnostics read back every 10 steps, final density read
+back); `roofline` relates the step kernel's algorithmic bytes to the measured
+HBM copy bandwidth; `cpu_baseline` times the FP64 reference implementation on
+a bounded slab of the same workload on the host cores.
+
+With N > 1 (torchrun) every rank advances its own replica of the ligament
+(weak scaling; the step has no data-path collective).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D3Q19 SC-LBM MLUPS & % HBM peak; FP32/FP16 & batched vs FP64 at stated error"
+BYTES_PER_POP = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--collision", choices=["srt", "mrt"], default="srt")
+    ap.add_argument("--storage", choices=list(BYTES_PER_POP), default="f32")
+    ap.add_argument("--R0", type=float, default=64.0)
+    ap.add_argument("--kR0", type=float, default=0.7)
+    ap.add_argument("--zchunk", type=int, default=0)
+    ap.add_argument("--tile-y", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_1905_09554_gb300 import inputs
+    nx, ny, nz = inputs.ligament_box(args.R0, args.kR0)
+    forcing = "shift" if args.collision == "srt" else "guo"
+    rl, rv = inputs.COEXISTENCE[(forcing, -5.5, 1.0)]
+    name = (f"ligament R0={args.R0:g} kR0={args.kR0:g} box {nx}x{ny}x{nz}, G=-5.5, "
+            f"{args.collision.upper()} tau=1, {args.storage.upper()} populations, 5% cosine perturbation")
+    return dict(nx=nx, ny=ny, nz=nz, rho_l=rl, rho_v=rv, name=name)
+
+
+def measured_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if bus_id:
+            cmd[1:1] = ["-i", bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.seek(0)
+        rows = [r.split(", ") for r in self.out.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.out.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# -------------------------------------------------------------- CPU oracle
+def oracle_mlups(w, args, slab, min_seconds, max_steps):
+    """FP64 reference step timed on the host cores on a z-slab (thickness
+    `slab`, periodic) of the workload's initial state.  Returns
+    (MLUPS, effective cores, description, steps)."""
+    import numpy as np
+
+    from oracle import lbm_oracle as o
+    from paper_1905_09554_gb300 import inputs
+    rho = inputs.ligament_density(w["nx"], w["ny"], slab, args.R0, 0.05, w["rho_l"], w["rho_v"])
+    p = o.Params(G=-5.5, tau=1.0, collision=args.collision)
+    f = o.init_populations(rho)
+    f = o.step(f, p)  # warm-up
+    t0, c0 = time.perf_counter(), os.times()
+    steps = 0
+    while steps < max_steps and (steps == 0 or time.perf_counter() - t0 < min_seconds):
+        f = o.step(f, p)
+        steps += 1
+    dt = time.perf_counter() - t0
+    c1 = os.times()
+    cpu = (c1.user - c0.user) + (c1.system - c0.system)
+    cells = rho.size
+    assert np.isfinite(f).all()
+    desc = (f"FP64 numpy reference, {steps} steps of a {w['nx']}x{w['ny']}x{slab} periodic z-slab of the "
+            f"workload's initial ligament ({cells} cells)")
+    return cells * steps / dt / 1e6, max(1, round(cpu / dt)), desc, steps
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(args)
+    # each step on a 1-cell-thick slab (65536 cells) keeps K+W steps within minutes
+    cells_xy = w["nx"] * w["ny"]
+    per_step = cells_xy * 1.5e-6
+    slab = max(1, min(16, int(150.0 / max(1, args.steps + args.warmup) / per_step)))
+    from oracle import lbm_oracle as o
+    from paper_1905_09554_gb300 import inputs
+    rho = inputs.ligament_density(w["nx"], w["ny"], slab, args.R0, 0.05, w["rho_l"], w["rho_v"])
+    p = o.Params(G=-5.5, tau=1.0, collision=args.collision)
+    f = o.init_populations(rho)
+    for _ in range(args.warmup):
+        f = o.step(f, p)
+    t0, c0 = time.perf_counter(), os.times()
+    for _ in range(args.steps):
+        f = o.step(f, p)
+    dt = time.perf_counter() - t0
+    c1 = os.times()
+    cores = max(1, round(((c1.user - c0.user) + (c1.system - c0.system)) / dt))
+    value = rho.size * args.steps / dt / 1e6
+    sample = (f"FP64 numpy reference; each step is a {w['nx']}x{w['ny']}x{slab} periodic z-slab "
+              f"({rho.size} cells) of the workload's initial ligament")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w["name"], "sample_cells": rho.size},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ------------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1905_09554_gb300 import lbm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = workload(args)
+    nx, ny, nz = w["nx"], w["ny"], w["nz"]
+    ncell = nx * ny * nz
+    L = lbm.Lattice(nx, ny, nz, G=-5.5, tau=1.0, collision=args.collision, storage=args.storage,
+                    zchunk=args.zchunk, tile_y=args.tile_y)
+    L.init_ligament(args.R0, 0.05, w["rho_l"], w["rho_v"])
+    stream = torch.cuda.current_stream()
+    d0 = L.diag(w["rho_l"], w["rho_v"])
+    L.step(args.warmup)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(local).pci_bus_id
+    except Exception:
+        bus = None
+    sampler = ClockSampler(bus) if rank == 0 else None
+    time.sleep(0.3 if sampler else 0)
+    t_start.record(stream)
+    for s, e in ev:
+        s.record(stream)
+        L.step(1)
+        e.record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    total_ms = t_start.elapsed_time(t_end)
+    kernel_ms = sum(s.elapsed_time(e) for s, e in ev) / args.steps
+    d1 = L.diag(w["rho_l"], w["rho_v"])
+    mass_drift = abs(d1["mass"] - d0["mass"]) / d0["mass"]
+
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * ncell * args.steps / (total_ms / 1e3) / 1e6
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        K = args.e2e_steps
+        rho_host = torch.empty((nz, ny, nx), dtype=torch.float64, pin_memory=True)
+        from paper_1905_09554_gb300 import inputs
+        rho_host.numpy()[...] = inputs.ligament_density(nx, ny, nz, args.R0, 0.05, w["rho_l"], w["rho_v"])
+        rho_out = torch.empty((nz, ny, nx), dtype=torch.float64, pin_memory=True)
+        diag_every = 10
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        L.set_density(rho_host.numpy())
+        for k in range(0, K, diag_every):
+            L.step(min(diag_every, K - k))
+            L.diag(w["rho_l"], w["rho_v"])
+        lbm.lbm_moments(L.ctx, rho_out.data_ptr(), None, None, None, 0)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        n_diag = (K + diag_every - 1) // diag_every
+        e2e = {"value": world * ncell * K / dt / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 8 * ncell / K,
+               "d2h_bytes_per_step": (8 * ncell + n_diag * 8 * (4 + 2 * nz)) / K,
+               "steps": K, "diag_every": diag_every}
+    L.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peak, src = measured_hbm()
+    bpc = 2 * 19 * BYTES_PER_POP[args.storage]
+    achieved = bpc * ncell / (kernel_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{src} HBM copy bandwidth",
+                "kernel": "sc_step_kernel", "algorithmic_bytes_per_cell": bpc,
+                "kernel_ms": kernel_ms}
+    traffic = load_traffic(args, ncell)
+    if traffic is not None:
+        roofline["traffic"] = traffic
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        mlups, cores, desc, _ = oracle_mlups(w, args, slab=16, min_seconds=10.0, max_steps=20)
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": desc}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+        "config": {"workload": w["name"], "cells": ncell, "collision": args.collision,
+                   "storage": args.storage, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (two population copies of "
+                         f"{19 * BYTES_PER_POP[args.storage] * ncell / 1e9:.2f} GB each)",
+                   "mass_rel_drift": mass_drift},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": args.steps,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def load_traffic(args, ncell):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current step kernel source and this storage/collision."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "step_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        rec = json.load(fh)
+    h = hashlib.sha256()
+    for f in ("step_kernel.cuh", "codec.cuh", "lattice.cuh"):
+        with open(os.path.join(ROOT, "paper_1905_09554_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    key = f"{args.collision}_{args.storage}"
+    if rec.get("kernel_sha256") != h.hexdigest() or key not in rec.get("bytes_per_cell", {}):
+        return None
+    return rec["bytes_per_cell"][key] * ncell
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,161 @@
+/*
+ * lbm_sc.h -- C ABI of the D3Q19 pseudo-potential (Shan-Chen) lattice
+ * Boltzmann step for one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Chiappini, Xue, Falcucci, Sbragaglia, "Hydrodynamic behavior of the
+ * Pseudo-Potential lattice Boltzmann method for interfacial flows"
+ * (arXiv:1905.09554), Sec. 2 (Eqs. LBE, local_eq, momentum, SC_force,
+ * vel_shift, barycentric) and the ligament set-up of Sec. 3.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - A field is nx*ny*nz values, x fastest: cell (x, y, z) sits at
+ *    index (z*ny + y)*nx + x.  Populations are 19 such fields, population a
+ *    at offset a*nx*ny*nz, in the order returned by lbm_velocities().
+ *  - The box is periodic in all three directions.
+ *  - The state at time t holds the post-streaming, pre-collision populations
+ *    f_a(x, t).  One step = Shan-Chen force, collision, streaming.
+ *  - Every call returns an lbm_status; none aborts or exits.  On failure the
+ *    context keeps a message (lbm_last_error).
+ *  - Pointers marked "host or device" are read/written on the host when
+ *    `on_device` is 0 and dereferenced by kernels when it is 1 (then they must
+ *    be device memory of the context's GPU, 8-byte aligned).  The caller owns
+ *    every array it passes; the library keeps no pointer to it after return.
+ *  - All work is ordered on the context's CUDA stream.  Calls that return
+ *    data to host memory synchronise that stream before returning; calls
+ *    that only enqueue work (lbm_step, device-side set/get) do not.
+ *  - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef LBM_SC_H
+#define LBM_SC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,        /* bad argument or parameter                      */
+    LBM_ENOMEM = 2,        /* device allocation failed                        */
+    LBM_ECUDA = 3,         /* a CUDA call or launch failed                    */
+    LBM_ENONFINITE = 4,    /* the diagnostics found rho <= 0, NaN or Inf      */
+    LBM_ETIMEOUT = 5,      /* a bounded device wait gave up                   */
+    LBM_EIO = 6,           /* file read/write or checksum failure             */
+    LBM_EUNSUPPORTED = 7   /* valid request this build does not provide       */
+} lbm_status;
+
+enum { LBM_D3Q19 = 0 };                        /* the only lattice (Sec. 2)   */
+enum { LBM_SRT_SHIFT = 0,                      /* SRT, velocity shift, Eq. vel_shift */
+       LBM_MRT_GUO = 1 };                      /* MRT, Guo-like forcing, Eq. barycentric */
+enum { LBM_PSI_EXP = 0 };                      /* psi = rho0 (1 - exp(-rho/rho0)), Sec. 2 */
+enum { LBM_F64 = 0,                            /* populations stored as double      */
+       LBM_F32 = 1,                            /* stored as float, float arithmetic */
+       LBM_F16_DEV = 2,                        /* half  deviations, float arithmetic */
+       LBM_BF16_DEV = 3 };                     /* bf16 deviations, float arithmetic  */
+
+typedef struct {
+    int lattice;          /* LBM_D3Q19                                              */
+    int nx, ny, nz;       /* periodic box, each >= 1                                */
+    double G;             /* interaction strength G0 of Eq. SC_force (< 0 attracts) */
+    int collision;        /* LBM_SRT_SHIFT or LBM_MRT_GUO                           */
+    double tau;           /* SRT relaxation time (> 0.5); MRT: shear rate = 1/tau   */
+    int has_rates;        /* MRT only: 1 = use s[] below, 0 = Sec. 2 rule           */
+    double s[19];         /* MRT rates in d'Humieres moment order (0-based):
+                             rho e eps jx qx jy qy jz qz 3pxx 3pixx pww piww pxy
+                             pyz pxz mx my mz.  Sec. 2 rule: e, 3pxx, pww, pxy,
+                             pyz, pxz relax at 1/tau, the rest at 1.              */
+    int psi;              /* LBM_PSI_EXP                                            */
+    double rho0;          /* reference density of psi (the paper fixes 1.0)        */
+    int storage;          /* LBM_F64 / LBM_F32 / LBM_F16_DEV / LBM_BF16_DEV          */
+    double rho_ref;       /* deviation storage: f_a = w_a rho_ref + d_a / dev_scale */
+    double dev_scale;     /* deviation storage scale (> 0)                          */
+    void *stream;         /* cudaStream_t for all work; NULL = legacy default       */
+    void *f_a, *f_b;      /* optional caller-owned device buffers for the two
+                             population copies (each 19*nx*ny*nz elements of the
+                             storage type, 16-byte aligned); NULL = the library
+                             allocates (and frees them in lbm_destroy).            */
+    int zchunk;           /* step kernel: z planes per thread block; 0 = auto       */
+    int tile_y;           /* step kernel: tile height (4, 8 or 16); 0 = auto        */
+} lbm_params;
+
+/* Fill *p with defaults: D3Q19, 32^3, G = -5.5, SRT tau = 1, psi exp, rho0 = 1,
+ * FP32 storage, rho_ref = 1, dev_scale = 1, default stream. */
+void lbm_params_default(lbm_params *p);
+
+/* Create a context on the current CUDA device.  Validates *p, allocates the
+ * population copies (unless given) and small diagnostic buffers, and leaves the
+ * populations zero.  On failure *out is NULL and lbm_last_error(NULL) returns
+ * the message. */
+lbm_status lbm_create(const lbm_params *p, lbm_ctx **out);
+
+/* Free everything the context allocated; NULL-safe. */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Message of the last failure on ctx (or of the last failed lbm_create on
+ * this thread when ctx is NULL); "" if none.  Owned by the library. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* The library's velocity order: c[3*a + i] is component i (x, y, z) of
+ * velocity a, w[a] its weight (D3Q19, Sec. 2).  Either pointer may be NULL. */
+lbm_status lbm_velocities(int c[57], double w[19]);
+
+/* Perturbed-ligament initial state (Sec. 3): a liquid cylinder along z
+ * through ((nx-1)/2, (ny-1)/2) with surface radius
+ * R(z) = R0 (1 + eps cos(2 pi n_waves z / nz)) and density
+ * rho = rho_v + (rho_l - rho_v)/2 (1 - tanh((r - R(z)) / width)); velocity
+ * zero, so f_a = w_a rho.  Resets the step counter. */
+lbm_status lbm_init_ligament(lbm_ctx *ctx, double R0, double eps, int n_waves,
+                             double width, double rho_l, double rho_v);
+
+/* State at rest with the given density field (host or device, float64,
+ * nx*ny*nz): f_a = w_a rho.  Resets the step counter. */
+lbm_status lbm_set_density(lbm_ctx *ctx, const double *rho, int on_device);
+
+/* Set / read all populations as float64 (host or device, 19*nx*ny*nz, library
+ * velocity order).  Storage conversion happens on the device. */
+lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f, int on_device);
+lbm_status lbm_get_populations(lbm_ctx *ctx, double *f, int on_device);
+
+/* Advance n >= 0 time steps (Eq. LBE): Shan-Chen force (Eq. SC_force with the
+ * psi law), SRT with the shifted equilibrium velocity u' = u + tau F / rho
+ * (Eq. vel_shift) or MRT with Guo-like forcing at u_b = u + F/(2 rho)
+ * (Eq. barycentric), then periodic streaming.  Enqueues n kernel launches. */
+lbm_status lbm_step(lbm_ctx *ctx, long n);
+
+/* Steps taken since the last initialisation. */
+long lbm_time(const lbm_ctx *ctx);
+
+/* Macroscopic fields of the current state (Eq. momentum): rho and the
+ * barycentric velocity u_b = (sum_a c_a f_a + F/2) / rho (Eq. barycentric),
+ * reported for both operators.  Each output (host or device, float64,
+ * nx*ny*nz) may be NULL to skip it. */
+lbm_status lbm_moments(lbm_ctx *ctx, double *rho, double *ux, double *uy,
+                       double *uz, int on_device);
+
+/* Ligament diagnostics of the current state, accumulated in float64 on the
+ * device, one thread block per z slice, deterministic:
+ *   mass     = sum rho                          (host, 1 value)
+ *   mom      = sum_a c_a f_a over the box        (host, 3 values)
+ *   area_z   = sum_xy clamp((rho - rho_v)/(rho_l - rho_v), 0, 1) per slice
+ *   maxrho_z = max_xy rho per slice              (host, nz values each)
+ * area_z/maxrho_z may be NULL.  rho_l/rho_v define the liquid fraction used
+ * for the neck radius R(z) = sqrt(area_z / pi) (Sec. 4).  Returns
+ * LBM_ENONFINITE if any cell has rho <= 0, NaN or Inf. */
+lbm_status lbm_diag(lbm_ctx *ctx, double rho_l, double rho_v, double *mass,
+                    double mom[3], double *area_z, double *maxrho_z);
+
+/* Select the CUDA stream (cudaStream_t) for later calls. */
+lbm_status lbm_set_stream(lbm_ctx *ctx, void *stream);
+
+/* Bytes of device memory the context allocated itself. */
+long long lbm_device_bytes(const lbm_ctx *ctx);
+
+/* sizeof(lbm_params) in this build, so that bindings can check their layout. */
+long long lbm_params_sizeof(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_SC_H */

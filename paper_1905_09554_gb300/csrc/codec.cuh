@@ -1,0 +1,102 @@
+// Storage codecs for the population arrays.  A codec names the stored type S,
+// the arithmetic type R and how one population is read and written.
+//
+//  F64: double storage, double arithmetic.
+//  F32: float storage, float arithmetic.
+//  F16Dev / BF16Dev: 16-bit storage of the deviation from the rest
+//     equilibrium at the reference density, d_a = (f_a - w_a rho_ref) * scale,
+//     decoded to float; arithmetic in float.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "lattice.cuh"
+
+namespace lbm {
+
+struct DevParams {
+    float rho_ref;
+    float scale;
+    float inv_scale;
+};
+
+struct CodecF64 {
+    using S = double;
+    using R = double;
+    static constexpr int kStorage = 0;
+    template <int q>
+    __device__ __forceinline__ static R load(const S* p, const DevParams&) { return __ldg(p); }
+    template <int q>
+    __device__ __forceinline__ static void store(S* p, R v, const DevParams&) { *p = v; }
+};
+
+struct CodecF32 {
+    using S = float;
+    using R = float;
+    static constexpr int kStorage = 1;
+    template <int q>
+    __device__ __forceinline__ static R load(const S* p, const DevParams&) { return __ldg(p); }
+    template <int q>
+    __device__ __forceinline__ static void store(S* p, R v, const DevParams&) { *p = v; }
+};
+
+struct CodecF16Dev {
+    using S = __half;
+    using R = float;
+    static constexpr int kStorage = 2;
+    template <int q>
+    __device__ __forceinline__ static R load(const S* p, const DevParams& d) {
+        return float(wq(q)) * d.rho_ref + __half2float(__ldg(p)) * d.inv_scale;
+    }
+    template <int q>
+    __device__ __forceinline__ static void store(S* p, R v, const DevParams& d) {
+        *p = __float2half_rn((v - float(wq(q)) * d.rho_ref) * d.scale);
+    }
+};
+
+struct CodecBF16Dev {
+    using S = __nv_bfloat16;
+    using R = float;
+    static constexpr int kStorage = 3;
+    template <int q>
+    __device__ __forceinline__ static R load(const S* p, const DevParams& d) {
+        return float(wq(q)) * d.rho_ref + __bfloat162float(__ldg(p)) * d.inv_scale;
+    }
+    template <int q>
+    __device__ __forceinline__ static void store(S* p, R v, const DevParams& d) {
+        *p = __float2bfloat16_rn((v - float(wq(q)) * d.rho_ref) * d.scale);
+    }
+};
+
+// Runtime (non-templated) decode/encode for the conversion kernels.
+template <class Codec>
+__device__ __forceinline__ double decode_rt(const typename Codec::S* p, float w, const DevParams& d);
+template <>
+__device__ __forceinline__ double decode_rt<CodecF64>(const double* p, float, const DevParams&) { return *p; }
+template <>
+__device__ __forceinline__ double decode_rt<CodecF32>(const float* p, float, const DevParams&) { return *p; }
+template <>
+__device__ __forceinline__ double decode_rt<CodecF16Dev>(const __half* p, float w, const DevParams& d) {
+    return double(w * d.rho_ref + __half2float(*p) * d.inv_scale);
+}
+template <>
+__device__ __forceinline__ double decode_rt<CodecBF16Dev>(const __nv_bfloat16* p, float w, const DevParams& d) {
+    return double(w * d.rho_ref + __bfloat162float(*p) * d.inv_scale);
+}
+
+template <class Codec>
+__device__ __forceinline__ void encode_rt(typename Codec::S* p, float w, double v, const DevParams& d);
+template <>
+__device__ __forceinline__ void encode_rt<CodecF64>(double* p, float, double v, const DevParams&) { *p = v; }
+template <>
+__device__ __forceinline__ void encode_rt<CodecF32>(float* p, float, double v, const DevParams&) { *p = float(v); }
+template <>
+__device__ __forceinline__ void encode_rt<CodecF16Dev>(__half* p, float w, double v, const DevParams& d) {
+    *p = __float2half_rn((float(v) - w * d.rho_ref) * d.scale);
+}
+template <>
+__device__ __forceinline__ void encode_rt<CodecBF16Dev>(__nv_bfloat16* p, float w, double v, const DevParams& d) {
+    *p = __float2bfloat16_rn((float(v) - w * d.rho_ref) * d.scale);
+}
+
+}  // namespace lbm

@@ -1,0 +1,686 @@
+// C ABI of the D3Q19 Shan-Chen lattice Boltzmann library (include/lbm_sc.h):
+// context management, initial states, the time-step driver, moments and
+// diagnostics.  The fused step kernel lives in step_kernel.cuh.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lbm_sc.h"
+#include "codec.cuh"
+#include "lattice.cuh"
+#include "step_kernel.cuh"
+
+using namespace lbm;
+
+struct lbm_ctx {
+    lbm_params p;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    void* f[2] = {nullptr, nullptr};  // population copies; f[cur] is the state
+    bool own_f = false;
+    int cur = 0;
+    long t = 0;
+    long long n = 0;
+    size_t elem = 0;                  // bytes per stored population
+    double* scratch = nullptr;        // staging / moments scratch (lazily grown)
+    size_t scratch_bytes = 0;
+    double* diag = nullptr;           // per-slice diagnostic partials (8 * nz)
+    std::vector<double> diag_host;
+    long long own_bytes = 0;
+    StepArgs args{};
+    int zchunk = 0, tile_y = 8;
+    char err[512] = {0};
+
+    lbm_status fail(lbm_status s, const char* fmt, ...) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(err, sizeof(err), fmt, ap);
+        va_end(ap);
+        return s;
+    }
+};
+
+static thread_local char g_create_err[512];
+
+#define LBM_CUDA(ctx, call)                                                                  \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return (ctx)->fail(e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA,     \
+                               "%s failed: %s", #call, cudaGetErrorString(e_));              \
+    } while (0)
+
+#define LBM_LAUNCHED(ctx, what)                                                              \
+    do {                                                                                     \
+        cudaError_t e_ = cudaGetLastError();                                                 \
+        if (e_ != cudaSuccess)                                                               \
+            return (ctx)->fail(LBM_ECUDA, "%s launch failed: %s", what, cudaGetErrorString(e_)); \
+    } while (0)
+
+// ----------------------------------------------------------------------------
+// Small kernels: initial states, conversions, moments, diagnostics.
+// ----------------------------------------------------------------------------
+namespace {
+
+// Weight of population q in the library order (rest, 6 axis, 12 edge).
+__device__ __forceinline__ float weight_rt(int q) {
+    return q == 0 ? float(1.0 / 3.0) : (q < 7 ? float(1.0 / 18.0) : float(1.0 / 36.0));
+}
+__device__ __forceinline__ double weight_rt_d(int q) {
+    return q == 0 ? 1.0 / 3.0 : (q < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+template <class Codec>
+__global__ void rest_state_kernel(typename Codec::S* __restrict__ f, const double* __restrict__ rho,
+                                  long long n, DevParams dev) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double r = rho[i];
+        for (int q = 0; q < Q; ++q)
+            encode_rt<Codec>(f + q * n + i, weight_rt(q), weight_rt_d(q) * r, dev);
+    }
+}
+
+template <class Codec>
+__global__ void ligament_kernel(typename Codec::S* __restrict__ f, int nx, int ny, int nz, double R0,
+                                double eps, int n_waves, double width, double rho_l, double rho_v,
+                                DevParams dev) {
+    const long long n = (long long)nx * ny * nz;
+    const double xc = 0.5 * (nx - 1), yc = 0.5 * (ny - 1);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = int(i % nx);
+        const int y = int((i / nx) % ny);
+        const int z = int(i / ((long long)nx * ny));
+        const double dx = x - xc, dy = y - yc;
+        const double r = sqrt(dx * dx + dy * dy);
+        const double R = R0 * (1.0 + eps * cos(two_pi * n_waves * z / nz));
+        const double rho = rho_v + 0.5 * (rho_l - rho_v) * (1.0 - tanh((r - R) / width));
+        for (int q = 0; q < Q; ++q)
+            encode_rt<Codec>(f + q * n + i, weight_rt(q), weight_rt_d(q) * rho, dev);
+    }
+}
+
+// Element i of `f` belongs to population q0 + i / n.
+template <class Codec>
+__global__ void decode_kernel(double* __restrict__ out, const typename Codec::S* __restrict__ f,
+                              long long count, long long n, int q0, DevParams dev) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = decode_rt<Codec>(f + i, weight_rt(q0 + int(i / n)), dev);
+}
+
+template <class Codec>
+__global__ void encode_kernel(typename Codec::S* __restrict__ f, const double* __restrict__ in,
+                              long long count, long long n, int q0, DevParams dev) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x)
+        encode_rt<Codec>(f + i, weight_rt(q0 + int(i / n)), in[i], dev);
+}
+
+template <class Codec>
+__global__ void density_kernel(double* __restrict__ rho, const typename Codec::S* __restrict__ f,
+                               long long n, DevParams dev) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double r = 0.0;
+        for (int q = 0; q < Q; ++q) r += decode_rt<Codec>(f + q * n + i, weight_rt(q), dev);
+        rho[i] = r;
+    }
+}
+
+// u_b = (j + F/2)/rho with F from Eq. SC_force evaluated on the density
+// field `rho` (float64), j from the populations.
+template <class Codec>
+__global__ void velocity_kernel(double* __restrict__ ux, double* __restrict__ uy, double* __restrict__ uz,
+                                const double* __restrict__ rho, const typename Codec::S* __restrict__ f,
+                                int nx, int ny, int nz, double G, double rho0, DevParams dev) {
+    const long long n = (long long)nx * ny * nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = int(i % nx);
+        const int y = int((i / nx) % ny);
+        const int z = int(i / ((long long)nx * ny));
+        double jx = 0, jy = 0, jz = 0, sx = 0, sy = 0, sz = 0;
+        static_for<0, Q>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            const double fq = decode_rt<Codec>(f + q * n + i, float(wq(q)), dev);
+            jx += cx(q) * fq;
+            jy += cy(q) * fq;
+            jz += cz(q) * fq;
+            if constexpr (q != 0) {
+                int xx = x + cx(q), yy = y + cy(q), zz = z + cz(q);
+                xx = xx < 0 ? nx - 1 : (xx == nx ? 0 : xx);
+                yy = yy < 0 ? ny - 1 : (yy == ny ? 0 : yy);
+                zz = zz < 0 ? nz - 1 : (zz == nz ? 0 : zz);
+                const double rn = rho[((long long)zz * ny + yy) * nx + xx];
+                const double psn = rho0 * (1.0 - exp(-rn / rho0));
+                sx += wq(q) * cx(q) * psn;
+                sy += wq(q) * cy(q) * psn;
+                sz += wq(q) * cz(q) * psn;
+            }
+        });
+        const double r = rho[i];
+        const double g = -G * rho0 * (1.0 - exp(-r / rho0));
+        if (ux) ux[i] = (jx + 0.5 * g * sx) / r;
+        if (uy) uy[i] = (jy + 0.5 * g * sy) / r;
+        if (uz) uz[i] = (jz + 0.5 * g * sz) / r;
+    }
+}
+
+// One block per z slice; fixed-order tree reduction in float64 (deterministic).
+// out[8*z + k]: k = 0 mass, 1..3 momentum, 4 liquid area, 5 max rho,
+// 6 count of cells with rho <= 0 or non-finite.
+constexpr int DIAG_THREADS = 256;
+
+template <class Codec>
+__global__ void __launch_bounds__(DIAG_THREADS)
+diag_kernel(double* __restrict__ out, const typename Codec::S* __restrict__ f, int nx, int ny,
+            long long n, double rho_l, double rho_v, DevParams dev) {
+    __shared__ double red[7][DIAG_THREADS];
+    const int z = blockIdx.x;
+    const long long plane = (long long)nx * ny;
+    const typename Codec::S* fz = f + z * plane;
+    double m = 0, jx = 0, jy = 0, jz = 0, area = 0, mx = 0, bad = 0;
+    const double inv = 1.0 / (rho_l - rho_v);
+    for (long long i = threadIdx.x; i < plane; i += DIAG_THREADS) {
+        double r = 0, ax = 0, ay = 0, az = 0;
+        static_for<0, Q>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            const double fq = decode_rt<Codec>(fz + q * n + i, float(wq(q)), dev);
+            r += fq;
+            ax += cx(q) * fq;
+            ay += cy(q) * fq;
+            az += cz(q) * fq;
+        });
+        m += r;
+        jx += ax;
+        jy += ay;
+        jz += az;
+        area += fmin(fmax((r - rho_v) * inv, 0.0), 1.0);
+        mx = fmax(mx, r);
+        if (!(r > 0.0) || !isfinite(r)) bad += 1.0;
+    }
+    red[0][threadIdx.x] = m;
+    red[1][threadIdx.x] = jx;
+    red[2][threadIdx.x] = jy;
+    red[3][threadIdx.x] = jz;
+    red[4][threadIdx.x] = area;
+    red[5][threadIdx.x] = mx;
+    red[6][threadIdx.x] = bad;
+    __syncthreads();
+    for (int s = DIAG_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            for (int k = 0; k < 7; ++k) {
+                if (k == 5) red[k][threadIdx.x] = fmax(red[k][threadIdx.x], red[k][threadIdx.x + s]);
+                else red[k][threadIdx.x] += red[k][threadIdx.x + s];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 7) out[8 * z + threadIdx.x] = red[threadIdx.x][0];
+}
+
+int grid_for(long long work, int threads, int num_sms) {
+    long long b = (work + threads - 1) / threads;
+    const long long cap = (long long)num_sms * 16;
+    if (b > cap) b = cap;
+    return int(b < 1 ? 1 : b);
+}
+
+// ----------------------------------------------------------------------------
+// Typed dispatch
+// ----------------------------------------------------------------------------
+template <class Codec, int COLL, int TY>
+cudaError_t launch_step_t(const lbm_ctx* c, const void* src, void* dst) {
+    constexpr int TX = 32;
+    const StepArgs& a = c->args;
+    dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + a.zchunk - 1) / a.zchunk);
+    sc_step_kernel<Codec, COLL, TX, TY><<<grid, TX * TY, 0, c->stream>>>(
+        static_cast<const typename Codec::S*>(src), static_cast<typename Codec::S*>(dst), a);
+    return cudaGetLastError();
+}
+
+template <class Codec, int COLL>
+cudaError_t launch_step_c(const lbm_ctx* c, const void* src, void* dst) {
+    switch (c->tile_y) {
+        case 4: return launch_step_t<Codec, COLL, 4>(c, src, dst);
+        case 16: return launch_step_t<Codec, COLL, 16>(c, src, dst);
+        default: return launch_step_t<Codec, COLL, 8>(c, src, dst);
+    }
+}
+
+template <class Codec>
+cudaError_t launch_step_s(const lbm_ctx* c, const void* src, void* dst) {
+    return c->p.collision == LBM_MRT_GUO ? launch_step_c<Codec, COLL_MRT>(c, src, dst)
+                                         : launch_step_c<Codec, COLL_SRT>(c, src, dst);
+}
+
+cudaError_t launch_step(const lbm_ctx* c, const void* src, void* dst) {
+    switch (c->p.storage) {
+        case LBM_F64: return launch_step_s<CodecF64>(c, src, dst);
+        case LBM_F16_DEV: return launch_step_s<CodecF16Dev>(c, src, dst);
+        case LBM_BF16_DEV: return launch_step_s<CodecBF16Dev>(c, src, dst);
+        default: return launch_step_s<CodecF32>(c, src, dst);
+    }
+}
+
+// Run `fn.template operator()<Codec>()` for the context's storage type.
+template <class Fn>
+auto with_codec(const lbm_ctx* c, Fn&& fn) {
+    switch (c->p.storage) {
+        case LBM_F64: return fn(CodecF64{});
+        case LBM_F16_DEV: return fn(CodecF16Dev{});
+        case LBM_BF16_DEV: return fn(CodecBF16Dev{});
+        default: return fn(CodecF32{});
+    }
+}
+
+lbm_status ensure_scratch(lbm_ctx* c, size_t bytes) {
+    if (c->scratch_bytes >= bytes) return LBM_OK;
+    if (c->scratch) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->scratch);
+        c->own_bytes -= (long long)c->scratch_bytes;
+        c->scratch = nullptr;
+        c->scratch_bytes = 0;
+    }
+    LBM_CUDA(c, cudaMalloc(&c->scratch, bytes));
+    c->scratch_bytes = bytes;
+    c->own_bytes += (long long)bytes;
+    return LBM_OK;
+}
+
+int auto_zchunk(const lbm_ctx* c) {
+    const long long xy_blocks = (long long)((c->p.nx + 31) / 32) * ((c->p.ny + c->tile_y - 1) / c->tile_y);
+    // Aim at ~4 blocks per SM in total so that the tail of the grid is short,
+    // with chunks no shorter than 16 planes (each chunk re-reads 2 planes).
+    const long long want_blocks = 4LL * c->num_sms;
+    long long chunks = (want_blocks + xy_blocks - 1) / xy_blocks;
+    if (chunks < 1) chunks = 1;
+    long long zc = (c->p.nz + chunks - 1) / chunks;
+    if (zc < 16) zc = 16;
+    if (zc > c->p.nz) zc = c->p.nz;
+    return int(zc);
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+// Public API
+// ----------------------------------------------------------------------------
+extern "C" {
+
+void lbm_params_default(lbm_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->lattice = LBM_D3Q19;
+    p->nx = p->ny = p->nz = 32;
+    p->G = -5.5;
+    p->collision = LBM_SRT_SHIFT;
+    p->tau = 1.0;
+    p->psi = LBM_PSI_EXP;
+    p->rho0 = 1.0;
+    p->storage = LBM_F32;
+    p->rho_ref = 1.0;
+    p->dev_scale = 1.0;
+}
+
+const char* lbm_last_error(const lbm_ctx* ctx) { return ctx ? ctx->err : g_create_err; }
+
+lbm_status lbm_velocities(int c[57], double w[19]) {
+    for (int q = 0; q < Q; ++q) {
+        if (c) {
+            c[3 * q + 0] = cx(q);
+            c[3 * q + 1] = cy(q);
+            c[3 * q + 2] = cz(q);
+        }
+        if (w) w[q] = wq(q);
+    }
+    return LBM_OK;
+}
+
+static lbm_status create_fail(lbm_status s, const char* msg) {
+    snprintf(g_create_err, sizeof(g_create_err), "%s", msg);
+    return s;
+}
+
+lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
+    g_create_err[0] = 0;
+    if (!out) return create_fail(LBM_EINVAL, "lbm_create: out is NULL");
+    *out = nullptr;
+    if (!p) return create_fail(LBM_EINVAL, "lbm_create: params is NULL");
+    if (p->lattice != LBM_D3Q19) return create_fail(LBM_EINVAL, "lbm_create: only D3Q19 is provided");
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return create_fail(LBM_EINVAL, "lbm_create: box sizes must be >= 1");
+    const long long n = (long long)p->nx * p->ny * p->nz;
+    if (n > (1LL << 40)) return create_fail(LBM_EINVAL, "lbm_create: box too large");
+    if (p->collision != LBM_SRT_SHIFT && p->collision != LBM_MRT_GUO)
+        return create_fail(LBM_EINVAL, "lbm_create: unknown collision operator");
+    if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return create_fail(LBM_EINVAL, "lbm_create: tau must be > 0.5");
+    if (!std::isfinite(p->G)) return create_fail(LBM_EINVAL, "lbm_create: G must be finite");
+    if (p->psi != LBM_PSI_EXP) return create_fail(LBM_EINVAL, "lbm_create: unknown psi law");
+    if (!(p->rho0 > 0) || !std::isfinite(p->rho0)) return create_fail(LBM_EINVAL, "lbm_create: rho0 must be > 0");
+    if (p->storage < LBM_F64 || p->storage > LBM_BF16_DEV) return create_fail(LBM_EINVAL, "lbm_create: unknown storage");
+    if (p->storage >= LBM_F16_DEV && (!(p->dev_scale > 0) || !std::isfinite(p->rho_ref)))
+        return create_fail(LBM_EINVAL, "lbm_create: deviation storage needs dev_scale > 0 and finite rho_ref");
+    if (p->collision == LBM_MRT_GUO && p->has_rates) {
+        for (int k = 0; k < Q; ++k)
+            if (!(p->s[k] > 0.0 && p->s[k] < 2.0))
+                return create_fail(LBM_EINVAL, "lbm_create: MRT rates must lie in (0, 2)");
+    }
+    if (p->tile_y != 0 && p->tile_y != 4 && p->tile_y != 8 && p->tile_y != 16)
+        return create_fail(LBM_EINVAL, "lbm_create: tile_y must be 0, 4, 8 or 16");
+    if (p->zchunk < 0) return create_fail(LBM_EINVAL, "lbm_create: zchunk must be >= 0");
+    if ((p->f_a == nullptr) != (p->f_b == nullptr))
+        return create_fail(LBM_EINVAL, "lbm_create: give both f_a and f_b or neither");
+    if (p->f_a && ((reinterpret_cast<uintptr_t>(p->f_a) | reinterpret_cast<uintptr_t>(p->f_b)) & 15))
+        return create_fail(LBM_EINVAL, "lbm_create: f_a/f_b must be 16-byte aligned");
+
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return create_fail(LBM_ENOMEM, "lbm_create: host allocation failed");
+    c->p = *p;
+    c->stream = static_cast<cudaStream_t>(p->stream);
+    c->n = n;
+    c->elem = p->storage == LBM_F64 ? 8 : (p->storage == LBM_F32 ? 4 : 2);
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        snprintf(g_create_err, sizeof(g_create_err), "lbm_create: no usable CUDA device: %s", cudaGetErrorString(e));
+        delete c;
+        return LBM_ECUDA;
+    }
+    const size_t fbytes = (size_t)Q * (size_t)n * c->elem;
+    if (p->f_a) {
+        c->f[0] = p->f_a;
+        c->f[1] = p->f_b;
+    } else {
+        c->own_f = true;
+        e = cudaMalloc(&c->f[0], fbytes);
+        if (e == cudaSuccess) e = cudaMalloc(&c->f[1], fbytes);
+        if (e != cudaSuccess) {
+            snprintf(g_create_err, sizeof(g_create_err), "lbm_create: population allocation of 2 x %zu bytes failed: %s",
+                     fbytes, cudaGetErrorString(e));
+            cudaFree(c->f[0]);
+            delete c;
+            return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+        }
+        c->own_bytes += 2 * (long long)fbytes;
+        cudaMemsetAsync(c->f[0], 0, fbytes, c->stream);
+        cudaMemsetAsync(c->f[1], 0, fbytes, c->stream);
+    }
+    e = cudaMalloc(&c->diag, sizeof(double) * 8 * (size_t)p->nz);
+    if (e != cudaSuccess) {
+        snprintf(g_create_err, sizeof(g_create_err), "lbm_create: diagnostics allocation failed: %s", cudaGetErrorString(e));
+        if (c->own_f) { cudaFree(c->f[0]); cudaFree(c->f[1]); }
+        delete c;
+        return LBM_ENOMEM;
+    }
+    c->own_bytes += (long long)(sizeof(double) * 8 * (size_t)p->nz);
+    c->diag_host.resize(8 * (size_t)p->nz);
+
+    // Kernel arguments.
+    StepArgs& a = c->args;
+    a.nx = p->nx;
+    a.ny = p->ny;
+    a.nz = p->nz;
+    a.n = n;
+    a.G = p->G;
+    a.tau = p->tau;
+    a.omega = 1.0 / p->tau;
+    a.rho0 = p->rho0;
+    a.inv_rho0 = 1.0 / p->rho0;
+    for (int k = 0; k < Q; ++k) a.s[k] = 1.0;
+    if (p->collision == LBM_MRT_GUO) {
+        if (p->has_rates) {
+            for (int k = 0; k < Q; ++k) a.s[k] = p->s[k];
+        } else {  // Sec. 2 rule: e, 3pxx, pww, pxy, pyz, pxz at 1/tau, others 1
+            const int rel[6] = {1, 9, 11, 13, 14, 15};
+            for (int k : rel) a.s[k] = 1.0 / p->tau;
+        }
+    }
+    a.dev.rho_ref = float(p->rho_ref);
+    a.dev.scale = float(p->dev_scale);
+    a.dev.inv_scale = float(1.0 / p->dev_scale);
+    c->tile_y = p->tile_y ? p->tile_y : 8;
+    c->zchunk = p->zchunk ? (p->zchunk < p->nz ? p->zchunk : p->nz) : auto_zchunk(c);
+    a.zchunk = c->zchunk;
+
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        snprintf(g_create_err, sizeof(g_create_err), "lbm_create: %s", cudaGetErrorString(e));
+        lbm_destroy(c);
+        return LBM_ECUDA;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    if (c->own_f) {
+        cudaFree(c->f[0]);
+        cudaFree(c->f[1]);
+    }
+    cudaFree(c->scratch);
+    cudaFree(c->diag);
+    delete c;
+}
+
+lbm_status lbm_set_stream(lbm_ctx* c, void* stream) {
+    if (!c) return LBM_EINVAL;
+    c->stream = static_cast<cudaStream_t>(stream);
+    return LBM_OK;
+}
+
+long lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
+
+long long lbm_device_bytes(const lbm_ctx* c) { return c ? c->own_bytes : 0; }
+
+long long lbm_params_sizeof(void) { return (long long)sizeof(lbm_params); }
+
+lbm_status lbm_init_ligament(lbm_ctx* c, double R0, double eps, int n_waves, double width, double rho_l,
+                             double rho_v) {
+    if (!c) return LBM_EINVAL;
+    if (!(R0 > 0) || !(width > 0) || !(rho_l > 0) || !(rho_v > 0) || !std::isfinite(eps) || n_waves < 0)
+        return c->fail(LBM_EINVAL, "lbm_init_ligament: need R0 > 0, width > 0, rho_l, rho_v > 0, n_waves >= 0");
+    const int blocks = grid_for(c->n, 256, c->num_sms);
+    const auto& p = c->p;
+    with_codec(c, [&](auto codec) {
+        using C = decltype(codec);
+        ligament_kernel<C><<<blocks, 256, 0, c->stream>>>(static_cast<typename C::S*>(c->f[c->cur]), p.nx, p.ny,
+                                                          p.nz, R0, eps, n_waves, width, rho_l, rho_v, c->args.dev);
+        return 0;
+    });
+    LBM_LAUNCHED(c, "ligament_kernel");
+    c->t = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_density(lbm_ctx* c, const double* rho, int on_device) {
+    if (!c) return LBM_EINVAL;
+    if (!rho) return c->fail(LBM_EINVAL, "lbm_set_density: rho is NULL");
+    const double* d_rho = rho;
+    if (!on_device) {
+        lbm_status s = ensure_scratch(c, sizeof(double) * (size_t)c->n);
+        if (s != LBM_OK) return s;
+        LBM_CUDA(c, cudaMemcpyAsync(c->scratch, rho, sizeof(double) * (size_t)c->n, cudaMemcpyHostToDevice, c->stream));
+        d_rho = c->scratch;
+    }
+    const int blocks = grid_for(c->n, 256, c->num_sms);
+    with_codec(c, [&](auto codec) {
+        using C = decltype(codec);
+        rest_state_kernel<C><<<blocks, 256, 0, c->stream>>>(static_cast<typename C::S*>(c->f[c->cur]), d_rho, c->n,
+                                                            c->args.dev);
+        return 0;
+    });
+    LBM_LAUNCHED(c, "rest_state_kernel");
+    if (!on_device) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->t = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_ctx* c, const double* f, int on_device) {
+    if (!c) return LBM_EINVAL;
+    if (!f) return c->fail(LBM_EINVAL, "lbm_set_populations: f is NULL");
+    if (on_device) {
+        with_codec(c, [&](auto codec) {
+            using C = decltype(codec);
+            encode_kernel<C><<<grid_for((long long)Q * c->n, 256, c->num_sms), 256, 0, c->stream>>>(
+                static_cast<typename C::S*>(c->f[c->cur]), f, (long long)Q * c->n, c->n, 0, c->args.dev);
+            return 0;
+        });
+        LBM_LAUNCHED(c, "encode_kernel");
+    } else {
+        // One population at a time through an n-double staging buffer.
+        lbm_status s = ensure_scratch(c, sizeof(double) * (size_t)c->n);
+        if (s != LBM_OK) return s;
+        const int blocks = grid_for(c->n, 256, c->num_sms);
+        for (int q = 0; q < Q; ++q) {
+            LBM_CUDA(c, cudaMemcpyAsync(c->scratch, f + (size_t)q * c->n, sizeof(double) * (size_t)c->n,
+                                        cudaMemcpyHostToDevice, c->stream));
+            with_codec(c, [&](auto codec) {
+                using C = decltype(codec);
+                encode_kernel<C><<<blocks, 256, 0, c->stream>>>(
+                    static_cast<typename C::S*>(c->f[c->cur]) + (size_t)q * c->n, c->scratch, c->n, c->n, q,
+                    c->args.dev);
+                return 0;
+            });
+            LBM_LAUNCHED(c, "encode_kernel");
+        }
+        LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    c->t = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_ctx* c, double* f, int on_device) {
+    if (!c) return LBM_EINVAL;
+    if (!f) return c->fail(LBM_EINVAL, "lbm_get_populations: f is NULL");
+    if (on_device) {
+        with_codec(c, [&](auto codec) {
+            using C = decltype(codec);
+            decode_kernel<C><<<grid_for((long long)Q * c->n, 256, c->num_sms), 256, 0, c->stream>>>(
+                f, static_cast<const typename C::S*>(c->f[c->cur]), (long long)Q * c->n, c->n, 0, c->args.dev);
+            return 0;
+        });
+        LBM_LAUNCHED(c, "decode_kernel");
+        return LBM_OK;
+    }
+    lbm_status s = ensure_scratch(c, sizeof(double) * (size_t)c->n);
+    if (s != LBM_OK) return s;
+    const int blocks = grid_for(c->n, 256, c->num_sms);
+    for (int q = 0; q < Q; ++q) {
+        with_codec(c, [&](auto codec) {
+            using C = decltype(codec);
+            decode_kernel<C><<<blocks, 256, 0, c->stream>>>(
+                c->scratch, static_cast<const typename C::S*>(c->f[c->cur]) + (size_t)q * c->n, c->n, c->n, q,
+                c->args.dev);
+            return 0;
+        });
+        LBM_LAUNCHED(c, "decode_kernel");
+        LBM_CUDA(c, cudaMemcpyAsync(f + (size_t)q * c->n, c->scratch, sizeof(double) * (size_t)c->n,
+                                    cudaMemcpyDeviceToHost, c->stream));
+        LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* c, long nsteps) {
+    if (!c) return LBM_EINVAL;
+    if (nsteps < 0) return c->fail(LBM_EINVAL, "lbm_step: n must be >= 0");
+    for (long k = 0; k < nsteps; ++k) {
+        cudaError_t e = launch_step(c, c->f[c->cur], c->f[c->cur ^ 1]);
+        if (e != cudaSuccess) return c->fail(LBM_ECUDA, "step kernel launch failed: %s", cudaGetErrorString(e));
+        c->cur ^= 1;
+        ++c->t;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_ctx* c, double* rho, double* ux, double* uy, double* uz, int on_device) {
+    if (!c) return LBM_EINVAL;
+    const size_t nb = sizeof(double) * (size_t)c->n;
+    double *d_rho, *d_ux, *d_uy, *d_uz;
+    if (on_device) {
+        lbm_status s = rho ? LBM_OK : ensure_scratch(c, nb);
+        if (s != LBM_OK) return s;
+        d_rho = rho ? rho : c->scratch;
+        d_ux = ux;
+        d_uy = uy;
+        d_uz = uz;
+    } else {
+        lbm_status s = ensure_scratch(c, 4 * nb);
+        if (s != LBM_OK) return s;
+        d_rho = c->scratch;
+        d_ux = ux ? c->scratch + c->n : nullptr;
+        d_uy = uy ? c->scratch + 2 * c->n : nullptr;
+        d_uz = uz ? c->scratch + 3 * c->n : nullptr;
+    }
+    const int blocks = grid_for(c->n, 256, c->num_sms);
+    const auto& p = c->p;
+    with_codec(c, [&](auto codec) {
+        using C = decltype(codec);
+        const auto* f = static_cast<const typename C::S*>(c->f[c->cur]);
+        density_kernel<C><<<blocks, 256, 0, c->stream>>>(d_rho, f, c->n, c->args.dev);
+        if (d_ux || d_uy || d_uz)
+            velocity_kernel<C><<<blocks, 256, 0, c->stream>>>(d_ux, d_uy, d_uz, d_rho, f, p.nx, p.ny, p.nz, p.G,
+                                                              p.rho0, c->args.dev);
+        return 0;
+    });
+    LBM_LAUNCHED(c, "moments kernels");
+    if (!on_device) {
+        if (rho) LBM_CUDA(c, cudaMemcpyAsync(rho, d_rho, nb, cudaMemcpyDeviceToHost, c->stream));
+        if (ux) LBM_CUDA(c, cudaMemcpyAsync(ux, d_ux, nb, cudaMemcpyDeviceToHost, c->stream));
+        if (uy) LBM_CUDA(c, cudaMemcpyAsync(uy, d_uy, nb, cudaMemcpyDeviceToHost, c->stream));
+        if (uz) LBM_CUDA(c, cudaMemcpyAsync(uz, d_uz, nb, cudaMemcpyDeviceToHost, c->stream));
+        LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_diag(lbm_ctx* c, double rho_l, double rho_v, double* mass, double mom[3], double* area_z,
+                    double* maxrho_z) {
+    if (!c) return LBM_EINVAL;
+    if (!(rho_l > rho_v)) return c->fail(LBM_EINVAL, "lbm_diag: need rho_l > rho_v");
+    const auto& p = c->p;
+    with_codec(c, [&](auto codec) {
+        using C = decltype(codec);
+        diag_kernel<C><<<p.nz, DIAG_THREADS, 0, c->stream>>>(
+            c->diag, static_cast<const typename C::S*>(c->f[c->cur]), p.nx, p.ny, c->n, rho_l, rho_v, c->args.dev);
+        return 0;
+    });
+    LBM_LAUNCHED(c, "diag_kernel");
+    LBM_CUDA(c, cudaMemcpyAsync(c->diag_host.data(), c->diag, sizeof(double) * 8 * (size_t)p.nz,
+                                cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    double m = 0, jx = 0, jy = 0, jz = 0, bad = 0;
+    for (int z = 0; z < p.nz; ++z) {
+        const double* d = &c->diag_host[8 * (size_t)z];
+        m += d[0];
+        jx += d[1];
+        jy += d[2];
+        jz += d[3];
+        bad += d[6];
+        if (area_z) area_z[z] = d[4];
+        if (maxrho_z) maxrho_z[z] = d[5];
+    }
+    if (mass) *mass = m;
+    if (mom) {
+        mom[0] = jx;
+        mom[1] = jy;
+        mom[2] = jz;
+    }
+    if (bad > 0 || !std::isfinite(m))
+        return c->fail(LBM_ENONFINITE, "lbm_diag: %.0f cells with rho <= 0 or non-finite at step %ld", bad, c->t);
+    return LBM_OK;
+}
+
+}  // extern "C"

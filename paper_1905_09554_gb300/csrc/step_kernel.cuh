@@ -1,0 +1,300 @@
+// The fused Shan-Chen D3Q19 time step (Sec. 2 of arXiv:1905.09554):
+// pseudo-potential psi(rho), single-belt force (Eq. SC_force), SRT with the
+// shifted equilibrium velocity (Eq. vel_shift) or MRT with Guo-like forcing at
+// the barycentric velocity (Eq. barycentric), and periodic streaming
+// (Eq. LBE), in ONE kernel launch per step.
+//
+// Design (push scheme, 2.5D z-march):
+//  * The state holds post-streaming populations f_a(x, t), SoA
+//    f[a][z][y][x].  A cell's density needs only its own 19 values, so every
+//    population load is aligned and coalesced.
+//  * A thread block owns a TX x TY column of cells and walks a chunk of z
+//    planes.  For each plane it loads the 19 populations of its cells into
+//    registers, turns rho into psi in shared memory, and also computes psi on
+//    the one-cell ring around the tile (those loads are other blocks' cells
+//    of the same plane and are normally served by L2).  A ring of four psi
+//    planes lets the block collide plane z once plane z+1 is in, with one
+//    barrier per plane.  psi never goes to HBM.
+//  * After the collision each cell pushes f*_a to x + c_a in the other copy.
+// HBM traffic per cell update is therefore one read and one write of the 19
+// populations plus the halo/chunk re-reads that miss L2.
+#pragma once
+#include <cstdint>
+
+#include "codec.cuh"
+#include "lattice.cuh"
+
+namespace lbm {
+
+enum { COLL_SRT = 0, COLL_MRT = 1 };
+
+struct StepArgs {
+    int nx, ny, nz;
+    int zchunk;           // planes per block along z
+    long long n;          // cells = nx*ny*nz (population stride)
+    double G;             // interaction strength G0
+    double tau, omega;    // SRT relaxation time and 1/tau
+    double rho0, inv_rho0;
+    double s[Q];          // MRT rates, moment order
+    DevParams dev;
+};
+
+template <class R>
+__device__ __forceinline__ R psi_of(R rho, R rho0, R inv_rho0);
+template <>
+__device__ __forceinline__ double psi_of<double>(double rho, double rho0, double inv_rho0) {
+    return rho0 * (1.0 - exp(-rho * inv_rho0));
+}
+template <>
+__device__ __forceinline__ float psi_of<float>(float rho, float rho0, float inv_rho0) {
+    return rho0 * (1.0f - expf(-rho * inv_rho0));
+}
+
+__device__ __forceinline__ int wrap_index(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+// SRT with shifted equilibrium (Eq. vel_shift): u' = (j + tau F)/rho,
+// f* = f + (f_eq(rho, u') - f)/tau.
+template <class R>
+__device__ __forceinline__ void collide_srt(R (&f)[Q], R Fx, R Fy, R Fz, R tau, R omega) {
+    R rho = R(0), jx = R(0), jy = R(0), jz = R(0);
+    static_for<0, Q>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        rho += f[q];
+        if constexpr (cx(q) != 0) jx += R(cx(q)) * f[q];
+        if constexpr (cy(q) != 0) jy += R(cy(q)) * f[q];
+        if constexpr (cz(q) != 0) jz += R(cz(q)) * f[q];
+    });
+    const R inv_rho = R(1) / rho;
+    const R ux = (jx + tau * Fx) * inv_rho;
+    const R uy = (jy + tau * Fy) * inv_rho;
+    const R uz = (jz + tau * Fz) * inv_rho;
+    const R usq = R(1.5) * (ux * ux + uy * uy + uz * uz);
+    static_for<0, Q>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        R cu = R(0);
+        if constexpr (cx(q) != 0) cu += R(cx(q)) * ux;
+        if constexpr (cy(q) != 0) cu += R(cy(q)) * uy;
+        if constexpr (cz(q) != 0) cu += R(cz(q)) * uz;
+        const R feq = R(wq(q)) * rho * (R(1) + R(3) * cu + R(4.5) * cu * cu - usq);
+        f[q] += omega * (feq - f[q]);
+    });
+}
+
+// MRT with Guo-like forcing (Eq. barycentric), d'Humieres D3Q19 basis:
+// m = M f, u_b = (j + F/2)/rho,
+// f* = f - M^-1 [ Lambda (m - m_eq(rho, u_b)) - (I - Lambda/2) M S ],
+// with the closed forms of m_eq = M f_eq and of the Guo source moments M S.
+// Conserved moments: the rho row vanishes and the j rows reduce to -F.
+template <class R>
+__device__ __forceinline__ void collide_mrt(R (&f)[Q], R Fx, R Fy, R Fz, const double (&s)[Q]) {
+    R m[Q];
+    static_for<0, Q>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        R acc = R(0);
+        static_for<0, Q>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            constexpr int c = mrt_coef(k, q);
+            if constexpr (c == 1) acc += f[q];
+            else if constexpr (c == -1) acc -= f[q];
+            else if constexpr (c != 0) acc += R(c) * f[q];
+        });
+        m[k] = acc;
+    });
+    const R rho = m[0];
+    const R inv_rho = R(1) / rho;
+    const R ux = (m[3] + R(0.5) * Fx) * inv_rho;
+    const R uy = (m[5] + R(0.5) * Fy) * inv_rho;
+    const R uz = (m[7] + R(0.5) * Fz) * inv_rho;
+    const R ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+    const R u2 = ux2 + uy2 + uz2;
+    const R uF = ux * Fx + uy * Fy + uz * Fz;
+    const R pxx = R(2) * ux2 - uy2 - uz2, pww = uy2 - uz2;
+    const R gxx = R(2) * ux * Fx - uy * Fy - uz * Fz, gww = uy * Fy - uz * Fz;
+
+    R meq[Q], sg[Q];
+    meq[1] = rho * (R(-11) + R(19) * u2);         sg[1] = R(38) * uF;
+    meq[2] = rho * (R(3) - R(5.5) * u2);          sg[2] = R(-11) * uF;
+    meq[4] = R(-2.0 / 3.0) * rho * ux;            sg[4] = R(-2.0 / 3.0) * Fx;
+    meq[6] = R(-2.0 / 3.0) * rho * uy;            sg[6] = R(-2.0 / 3.0) * Fy;
+    meq[8] = R(-2.0 / 3.0) * rho * uz;            sg[8] = R(-2.0 / 3.0) * Fz;
+    meq[9] = rho * pxx;                           sg[9] = R(2) * gxx;
+    meq[10] = R(-0.5) * rho * pxx;                sg[10] = -gxx;
+    meq[11] = rho * pww;                          sg[11] = R(2) * gww;
+    meq[12] = R(-0.5) * rho * pww;                sg[12] = -gww;
+    meq[13] = rho * ux * uy;                      sg[13] = ux * Fy + uy * Fx;
+    meq[14] = rho * uy * uz;                      sg[14] = uy * Fz + uz * Fy;
+    meq[15] = rho * ux * uz;                      sg[15] = ux * Fz + uz * Fx;
+    meq[16] = R(0);                               sg[16] = R(0);
+    meq[17] = R(0);                               sg[17] = R(0);
+    meq[18] = R(0);                               sg[18] = R(0);
+
+    // d[k] = (Lambda (m - m_eq) - (I - Lambda/2) S)_k / norm_k
+    R d[Q];
+    d[0] = R(0);
+    d[3] = -Fx * R(1.0 / mrt_norm(3));
+    d[5] = -Fy * R(1.0 / mrt_norm(5));
+    d[7] = -Fz * R(1.0 / mrt_norm(7));
+    static_for<0, Q>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        if constexpr (k != 0 && k != 3 && k != 5 && k != 7) {
+            const R sk = R(s[k]);
+            d[k] = (sk * (m[k] - meq[k]) - (R(1) - R(0.5) * sk) * sg[k]) * R(1.0 / mrt_norm(k));
+        }
+    });
+    static_for<0, Q>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        R acc = R(0);
+        static_for<1, Q>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            constexpr int c = mrt_coef(k, q);
+            if constexpr (c == 1) acc += d[k];
+            else if constexpr (c == -1) acc -= d[k];
+            else if constexpr (c != 0) acc += R(c) * d[k];
+        });
+        f[q] -= acc;
+    });
+}
+
+template <class Codec>
+__device__ __forceinline__ typename Codec::R cell_density(const typename Codec::S* __restrict__ p,
+                                                          long long n, const DevParams& dev) {
+    using R = typename Codec::R;
+    R r = R(0);
+    static_for<0, Q>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        r += Codec::template load<q>(p + q * n, dev);
+    });
+    return r;
+}
+
+template <class Codec, int COLL, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY)
+sc_step_kernel(const typename Codec::S* __restrict__ src, typename Codec::S* __restrict__ dst,
+               const StepArgs a) {
+    using R = typename Codec::R;
+    constexpr int PX = TX + 2, PY = TY + 2, PLANE = PX * PY, NSLOT = 4;
+    constexpr int NHALO = 2 * PX + 2 * TY;
+    static_assert(NHALO <= TX * TY, "tile too small for its halo ring");
+    __shared__ R psi_s[NSLOT][PLANE];
+
+    const int tid = threadIdx.x;
+    const int lx = tid % TX, ly = tid / TX;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const long long n = a.n;
+    const long long plane = (long long)nx * ny;
+    const int zs = blockIdx.z * a.zchunk;
+    if (zs >= nz) return;  // uniform over the block
+    const int ze = min(zs + a.zchunk, nz);
+
+    // Own cell (wrapped so that threads past a ragged edge still fill psi).
+    const int gx = wrap_index(x0 + lx, nx), gy = wrap_index(y0 + ly, ny);
+    const bool active = (x0 + lx < nx) && (y0 + ly < ny);
+    const int my_slot = (ly + 1) * PX + (lx + 1);
+    const long long my_xy = (long long)gy * nx + gx;
+
+    // Ring cell handled by this thread, if any.
+    int h_slot = -1;
+    long long h_xy = 0;
+    if (tid < NHALO) {
+        int hx, hy;
+        if (tid < PX) { hx = tid - 1; hy = -1; }
+        else if (tid < 2 * PX) { hx = tid - PX - 1; hy = TY; }
+        else { const int k = tid - 2 * PX; hx = (k < TY) ? -1 : TX; hy = (k < TY) ? k : k - TY; }
+        h_slot = (hy + 1) * PX + (hx + 1);
+        h_xy = (long long)wrap_index(y0 + hy, ny) * nx + wrap_index(x0 + hx, nx);
+    }
+
+    // Push targets in x and y (periodic).
+    const int xp = (gx + 1 == nx) ? 0 : gx + 1, xm = (gx == 0) ? nx - 1 : gx - 1;
+    const int yp = (gy + 1 == ny) ? 0 : gy + 1, ym = (gy == 0) ? ny - 1 : gy - 1;
+    const long long yoff[3] = {(long long)ym * nx, (long long)gy * nx, (long long)yp * nx};
+    const int xidx[3] = {xm, gx, xp};
+
+    const R rho0 = R(a.rho0), inv_rho0 = R(a.inv_rho0);
+    const R G = R(a.G), tau = R(a.tau), omega = R(a.omega);
+    const DevParams dev = a.dev;
+
+    auto slot_of = [&](int z) { return (z - zs + 1) & (NSLOT - 1); };
+
+    // Prologue: psi of plane zs-1, then populations and psi of plane zs.
+    {
+        const int zm = (zs == 0) ? nz - 1 : zs - 1;
+        const long long zo = (long long)zm * plane;
+        psi_s[slot_of(zs - 1)][my_slot] =
+            psi_of<R>(cell_density<Codec>(src + zo + my_xy, n, dev), rho0, inv_rho0);
+        if (h_slot >= 0)
+            psi_s[slot_of(zs - 1)][h_slot] =
+                psi_of<R>(cell_density<Codec>(src + zo + h_xy, n, dev), rho0, inv_rho0);
+    }
+    R fc[Q];
+    {
+        const long long zo = (long long)zs * plane;
+        R r = R(0);
+        static_for<0, Q>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            fc[q] = Codec::template load<q>(src + q * n + zo + my_xy, dev);
+            r += fc[q];
+        });
+        psi_s[slot_of(zs)][my_slot] = psi_of<R>(r, rho0, inv_rho0);
+        if (h_slot >= 0)
+            psi_s[slot_of(zs)][h_slot] =
+                psi_of<R>(cell_density<Codec>(src + zo + h_xy, n, dev), rho0, inv_rho0);
+    }
+
+    for (int z = zs; z < ze; ++z) {
+        const int zn = (z + 1 == nz) ? 0 : z + 1;
+        const int zp_slot = slot_of(z + 1);
+        R fn[Q];
+        {
+            const long long zo = (long long)zn * plane;
+            R r = R(0);
+            static_for<0, Q>([&](auto qc) {
+                constexpr int q = decltype(qc)::value;
+                fn[q] = Codec::template load<q>(src + q * n + zo + my_xy, dev);
+                r += fn[q];
+            });
+            psi_s[zp_slot][my_slot] = psi_of<R>(r, rho0, inv_rho0);
+            if (h_slot >= 0)
+                psi_s[zp_slot][h_slot] =
+                    psi_of<R>(cell_density<Codec>(src + zo + h_xy, n, dev), rho0, inv_rho0);
+        }
+        __syncthreads();
+
+        if (active) {
+            const R* pl[3] = {psi_s[slot_of(z - 1)], psi_s[slot_of(z)], psi_s[zp_slot]};
+            // Eq. SC_force: F = -G psi(x) sum_a w_a psi(x + c_a) c_a.
+            R sx = R(0), sy = R(0), sz = R(0);
+            static_for<1, Q>([&](auto qc) {
+                constexpr int q = decltype(qc)::value;
+                const R v = pl[cz(q) + 1][my_slot + cx(q) + cy(q) * PX];
+                if constexpr (cx(q) != 0) sx += R(wq(q) * cx(q)) * v;
+                if constexpr (cy(q) != 0) sy += R(wq(q) * cy(q)) * v;
+                if constexpr (cz(q) != 0) sz += R(wq(q) * cz(q)) * v;
+            });
+            const R gpsi = -G * pl[1][my_slot];
+            const R Fx = gpsi * sx, Fy = gpsi * sy, Fz = gpsi * sz;
+
+            if constexpr (COLL == COLL_SRT) collide_srt<R>(fc, Fx, Fy, Fz, tau, omega);
+            else collide_mrt<R>(fc, Fx, Fy, Fz, a.s);
+
+            // Eq. LBE streaming: f_a(x + c_a, t + 1) = f*_a(x, t).
+            const int zm = (z == 0) ? nz - 1 : z - 1;
+            const long long zoff[3] = {(long long)zm * plane, (long long)z * plane, (long long)zn * plane};
+            static_for<0, Q>([&](auto qc) {
+                constexpr int q = decltype(qc)::value;
+                const long long idx = zoff[cz(q) + 1] + yoff[cy(q) + 1] + xidx[cx(q) + 1];
+                Codec::template store<q>(dst + q * n + idx, fc[q], dev);
+            });
+        }
+        static_for<0, Q>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            fc[q] = fn[q];
+        });
+    }
+}
+
+}  // namespace lbm

@@ -1,0 +1,328 @@
+"""Thin ctypes binding of the C ABI in include/lbm_sc.h.
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``liblbm_sc.so``.  If the library is missing or cannot be loaded, every entry
+point raises; there is no CPU fallback.
+
+The module-level functions carry the C names (``lbm_create``, ``lbm_step``
+...) and return the raw ``lbm_status``; :class:`Lattice` wraps a context,
+raises :class:`LbmError` on failure, and can keep the two population copies
+in PyTorch device memory on the current PyTorch stream.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "liblbm_sc.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "lbm_sc.h")
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_EIO, LBM_EUNSUPPORTED = range(8)
+STATUS_NAMES = ["LBM_OK", "LBM_EINVAL", "LBM_ENOMEM", "LBM_ECUDA", "LBM_ENONFINITE",
+                "LBM_ETIMEOUT", "LBM_EIO", "LBM_EUNSUPPORTED"]
+LBM_D3Q19 = 0
+LBM_SRT_SHIFT, LBM_MRT_GUO = 0, 1
+LBM_PSI_EXP = 0
+LBM_F64, LBM_F32, LBM_F16_DEV, LBM_BF16_DEV = 0, 1, 2, 3
+STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16_DEV, "bf16": LBM_BF16_DEV}
+STORAGE_BYTES = {LBM_F64: 8, LBM_F32: 4, LBM_F16_DEV: 2, LBM_BF16_DEV: 2}
+COLLISION = {"srt": LBM_SRT_SHIFT, "mrt": LBM_MRT_GUO}
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_int),
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("G", ctypes.c_double),
+        ("collision", ctypes.c_int),
+        ("tau", ctypes.c_double),
+        ("has_rates", ctypes.c_int),
+        ("s", ctypes.c_double * 19),
+        ("psi", ctypes.c_int),
+        ("rho0", ctypes.c_double),
+        ("storage", ctypes.c_int),
+        ("rho_ref", ctypes.c_double),
+        ("dev_scale", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
+        ("f_a", ctypes.c_void_p), ("f_b", ctypes.c_void_p),
+        ("zchunk", ctypes.c_int),
+        ("tile_y", ctypes.c_int),
+    ]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_SIGNATURES = {
+    "lbm_params_default": (None, [ctypes.POINTER(lbm_params)]),
+    "lbm_create": (ctypes.c_int, [ctypes.POINTER(lbm_params), ctypes.POINTER(_P)]),
+    "lbm_destroy": (None, [_P]),
+    "lbm_last_error": (ctypes.c_char_p, [_P]),
+    "lbm_velocities": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), _D]),
+    "lbm_init_ligament": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+    "lbm_set_density": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "lbm_set_populations": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "lbm_get_populations": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "lbm_step": (ctypes.c_int, [_P, ctypes.c_long]),
+    "lbm_time": (ctypes.c_long, [_P]),
+    "lbm_moments": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int]),
+    "lbm_diag": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _D, _D, _D, _D]),
+    "lbm_set_stream": (ctypes.c_int, [_P, _P]),
+    "lbm_device_bytes": (ctypes.c_longlong, [_P]),
+    "lbm_params_sizeof": (ctypes.c_longlong, []),
+}
+
+_lib = None
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions declared in include/lbm_sc.h."""
+    text = re.sub(r"/\*.*?\*/", "", open(path).read(), flags=re.S)
+    return sorted(set(re.findall(r"^\s*[A-Za-z_][\w\s\*]*?\b(lbm_\w+)\s*\(", text, flags=re.M)))
+
+
+def load(path: str | None = None):
+    """Load liblbm_sc.so (building it first if it is absent and nvcc exists)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        from . import build as _build
+        p = _build.build()
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if lib.lbm_params_sizeof() != ctypes.sizeof(lbm_params):
+        raise RuntimeError("lbm_params layout mismatch between binding and library")
+    if path is None:
+        _lib = lib
+    return lib
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+# ------------------------------------------------------------ C-named calls
+def lbm_params_default() -> lbm_params:
+    p = lbm_params()
+    load().lbm_params_default(ctypes.byref(p))
+    return p
+
+
+def lbm_create(p: lbm_params):
+    ctx = _P()
+    st = load().lbm_create(ctypes.byref(p), ctypes.byref(ctx))
+    return st, ctx
+
+
+def lbm_destroy(ctx):
+    load().lbm_destroy(ctx)
+
+
+def lbm_last_error(ctx=None) -> str:
+    return (load().lbm_last_error(ctx) or b"").decode()
+
+
+def lbm_velocities():
+    c = (ctypes.c_int * 57)()
+    w = (ctypes.c_double * 19)()
+    load().lbm_velocities(c, w)
+    return np.array(c[:], dtype=np.int64).reshape(19, 3), np.array(w[:])
+
+
+def lbm_init_ligament(ctx, R0, eps, n_waves, width, rho_l, rho_v):
+    return load().lbm_init_ligament(ctx, R0, eps, n_waves, width, rho_l, rho_v)
+
+
+def lbm_set_density(ctx, ptr, on_device):
+    return load().lbm_set_density(ctx, ptr, on_device)
+
+
+def lbm_set_populations(ctx, ptr, on_device):
+    return load().lbm_set_populations(ctx, ptr, on_device)
+
+
+def lbm_get_populations(ctx, ptr, on_device):
+    return load().lbm_get_populations(ctx, ptr, on_device)
+
+
+def lbm_step(ctx, n):
+    return load().lbm_step(ctx, n)
+
+
+def lbm_time(ctx):
+    return load().lbm_time(ctx)
+
+
+def lbm_moments(ctx, rho, ux, uy, uz, on_device):
+    return load().lbm_moments(ctx, rho, ux, uy, uz, on_device)
+
+
+def lbm_diag(ctx, rho_l, rho_v, mass, mom, area_z, maxrho_z):
+    return load().lbm_diag(ctx, rho_l, rho_v, mass, mom, area_z, maxrho_z)
+
+
+def lbm_set_stream(ctx, stream):
+    return load().lbm_set_stream(ctx, stream)
+
+
+def lbm_device_bytes(ctx):
+    return load().lbm_device_bytes(ctx)
+
+
+# ------------------------------------------------------------ object wrapper
+def _host_ptr(a: np.ndarray):
+    return a.ctypes.data_as(_P)
+
+
+class Lattice:
+    """One periodic D3Q19 Shan-Chen lattice on the current CUDA device.
+
+    collision: 'srt' (shifted velocity) or 'mrt' (Guo forcing); rates: None
+    (the paper's rule), or 19 MRT rates in moment order.  storage: 'f64',
+    'f32', 'f16' or 'bf16'.  With torch_buffers=True the two population
+    copies are torch.cuda tensors owned by this object and all work runs on
+    torch's current stream.
+    """
+
+    def __init__(self, nx, ny, nz, G=-5.5, tau=1.0, collision="srt", rates=None,
+                 storage="f32", rho0=1.0, rho_ref=1.0, dev_scale=1.0,
+                 torch_buffers=True, stream=None, zchunk=0, tile_y=0):
+        lib = load()
+        p = lbm_params_default()
+        p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
+        p.G, p.tau, p.rho0 = float(G), float(tau), float(rho0)
+        p.collision = COLLISION[collision]
+        if rates is not None:
+            p.has_rates = 1
+            for k, v in enumerate(rates):
+                p.s[k] = float(v)
+        p.storage = STORAGE[storage]
+        p.rho_ref, p.dev_scale = float(rho_ref), float(dev_scale)
+        p.zchunk, p.tile_y = int(zchunk), int(tile_y)
+        self.shape = (int(nz), int(ny), int(nx))
+        self.n = int(nx) * int(ny) * int(nz)
+        self.storage = storage
+        self._bufs = None
+        self._torch_stream = None
+        if stream is not None:
+            p.stream = int(stream)
+        if torch_buffers:
+            import torch
+            if not torch.cuda.is_available():
+                raise LbmError(LBM_ECUDA, "no CUDA device visible to torch")
+            nbytes = 19 * self.n * STORAGE_BYTES[p.storage]
+            self._bufs = [torch.empty(nbytes, dtype=torch.uint8, device="cuda") for _ in range(2)]
+            p.f_a, p.f_b = self._bufs[0].data_ptr(), self._bufs[1].data_ptr()
+            if stream is None:
+                self._torch_stream = torch.cuda.current_stream()
+                p.stream = self._torch_stream.cuda_stream
+        self.params = p
+        st, ctx = lbm_create(p)
+        if st != LBM_OK:
+            raise LbmError(st, lbm_last_error(None))
+        self.ctx = ctx
+        self._lib = lib
+
+    # -- helpers
+    def _check(self, st):
+        if st != LBM_OK:
+            raise LbmError(st, lbm_last_error(self.ctx))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lbm_destroy(self.ctx)
+            self.ctx = None
+        self._bufs = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def time(self):
+        return lbm_time(self.ctx)
+
+    # -- state
+    def init_ligament(self, R0, eps, rho_l, rho_v, width=2.0, n_waves=1):
+        self._check(lbm_init_ligament(self.ctx, R0, eps, n_waves, width, rho_l, rho_v))
+
+    def set_density(self, rho):
+        """rho: numpy float64 (nz, ny, nx) or a contiguous float64 CUDA tensor."""
+        if isinstance(rho, np.ndarray):
+            a = np.ascontiguousarray(rho, dtype=np.float64)
+            assert a.size == self.n
+            self._check(lbm_set_density(self.ctx, _host_ptr(a), 0))
+        else:
+            assert rho.is_cuda and rho.numel() == self.n and rho.is_contiguous()
+            self._check(lbm_set_density(self.ctx, rho.data_ptr(), 1))
+
+    def set_populations(self, f):
+        if isinstance(f, np.ndarray):
+            a = np.ascontiguousarray(f, dtype=np.float64)
+            assert a.size == 19 * self.n
+            self._check(lbm_set_populations(self.ctx, _host_ptr(a), 0))
+        else:
+            assert f.is_cuda and f.numel() == 19 * self.n and f.is_contiguous()
+            self._check(lbm_set_populations(self.ctx, f.data_ptr(), 1))
+
+    def get_populations(self, out=None):
+        """float64 populations (19, nz, ny, nx), library velocity order; into
+        a CUDA tensor ``out`` if given, else a new numpy array."""
+        if out is not None:
+            assert out.is_cuda and out.numel() == 19 * self.n
+            self._check(lbm_get_populations(self.ctx, out.data_ptr(), 1))
+            return out
+        a = np.empty((19,) + self.shape)
+        self._check(lbm_get_populations(self.ctx, _host_ptr(a), 0))
+        return a
+
+    def step(self, n=1):
+        self._check(lbm_step(self.ctx, int(n)))
+
+    def moments(self):
+        """(rho, u) as numpy float64; u = (ux, uy, uz) barycentric."""
+        rho = np.empty(self.shape)
+        u = np.empty((3,) + self.shape)
+        self._check(lbm_moments(self.ctx, _host_ptr(rho), _host_ptr(u[0]), _host_ptr(u[1]),
+                                _host_ptr(u[2]), 0))
+        return rho, u
+
+    def moments_device(self, rho, ux=None, uy=None, uz=None):
+        ptr = lambda t: None if t is None else t.data_ptr()
+        self._check(lbm_moments(self.ctx, ptr(rho), ptr(ux), ptr(uy), ptr(uz), 1))
+
+    def diag(self, rho_l, rho_v, raise_nonfinite=True):
+        """dict(mass, mom (3,), area_z (nz,), maxrho_z (nz,), status)."""
+        nz = self.shape[0]
+        mass = ctypes.c_double()
+        mom = (ctypes.c_double * 3)()
+        area = np.empty(nz)
+        mx = np.empty(nz)
+        st = lbm_diag(self.ctx, rho_l, rho_v, ctypes.byref(mass), mom,
+                      area.ctypes.data_as(_D), mx.ctypes.data_as(_D))
+        if st != LBM_OK and (raise_nonfinite or st != LBM_ENONFINITE):
+            self._check(st)
+        return dict(mass=mass.value, mom=np.array(mom[:]), area_z=area, maxrho_z=mx, status=st)
+
+    def device_bytes(self):
+        return lbm_device_bytes(self.ctx)

@@ -1,0 +1,251 @@
+"""Parity of the CUDA step (through the C ABI) with the FP64 reference on the
+same seeded inputs.  Tolerances:
+
+* FP64 storage: 1e-12 max-abs on rho and u after 200 steps of the 32x32x64
+  ligament (and on smaller/ragged boxes), populations after one step 1e-13.
+* FP32 storage: 2e-5 max-abs on rho after 200 steps.
+* Tiling, z-chunking and block shape never change a FP64 result bit.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import lbm_oracle as o
+from paper_1905_09554_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - GPU machine only
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1905_09554_gb300 import lbm  # noqa: E402
+
+G = -5.5
+RL, RV = inputs.COEXISTENCE[("shift", G, 1.0)]
+RLG, RVG = inputs.COEXISTENCE[("guo", G, 1.0)]
+
+
+def perm():
+    """perm[a] = reference index of the library's velocity a."""
+    c, _ = lbm.lbm_velocities()
+    ref = {tuple(v): i for i, v in enumerate(o.C)}
+    return np.array([ref[tuple(v)] for v in c])
+
+
+def to_ref_order(f_lib):
+    out = np.empty_like(f_lib)
+    out[perm()] = f_lib
+    return out
+
+
+def to_lib_order(f_ref):
+    return f_ref[perm()]
+
+
+def oracle_run(rho, steps, G=G, tau=1.0, coll="srt", s=None):
+    p = o.Params(G=G, tau=tau, collision=coll, s=s)
+    f = o.run(o.init_populations(rho), steps, p)
+    r, u = o.macroscopic(f, p)
+    return f, r, u, p
+
+
+def gpu_run(rho, steps, storage="f64", coll="srt", tau=1.0, rates=None, G=G, **kw):
+    nz, ny, nx = rho.shape
+    with lbm.Lattice(nx, ny, nz, G=G, tau=tau, collision=coll, rates=rates, storage=storage, **kw) as L:
+        L.set_density(rho)
+        L.step(steps)
+        r, u = L.moments()
+        f = L.get_populations()
+        assert L.time == steps
+    return f, r, u
+
+
+@pytest.fixture(scope="module")
+def cfg_small():
+    """32x32x64 ligament, R0 = 8, 5% cosine perturbation, SRT tau = 1,
+    G = -5.5; reference after 200 steps."""
+    rho = inputs.ligament_density(32, 32, 64, 8.0, 0.05, RL, RV)
+    f, r, u, _ = oracle_run(rho, 200)
+    return rho, r, u
+
+
+def test_fp64_srt_ligament_200_steps(cfg_small):
+    rho0, r_ref, u_ref = cfg_small
+    _, r, u = gpu_run(rho0, 200, "f64")
+    assert np.abs(r - r_ref).max() <= 1e-12
+    assert np.abs(u - u_ref).max() <= 1e-12
+
+
+def test_fp32_srt_ligament_200_steps(cfg_small):
+    rho0, r_ref, u_ref = cfg_small
+    _, r, u = gpu_run(rho0, 200, "f32")
+    assert np.abs(r - r_ref).max() <= 2e-5
+    assert np.abs(u - u_ref).max() <= 2e-5
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 2e-5)])
+def test_mrt_shear_rates_ragged_box(storage, tol):
+    """MRT with Guo forcing, shear moments at 1/tau = 1.25, bulk and ghosts at
+    1; a box that is not a multiple of any tile (37 x 21 x 19)."""
+    rho = inputs.noisy_ligament_density(37, 21, 19, 4.0, 0.08, RLG, RVG, 1e-3, seed=11)
+    s = o.mrt_rates(0.8, rule="shear")
+    _, r_ref, u_ref, _ = oracle_run(rho, 60, tau=0.8, coll="mrt", s=s)
+    _, r, u = gpu_run(rho, 60, storage, coll="mrt", tau=0.8, rates=s)
+    assert np.abs(r - r_ref).max() <= tol
+    if storage == "f64":
+        assert np.abs(u - u_ref).max() <= tol
+
+
+def test_fp64_mrt_paper_rates_at_tau_not_one():
+    """Sec. 2 rate rule at tau = 0.7 (bulk and shear at 1/tau, ghosts 1), where
+    MRT differs from BGK, G = -5.3."""
+    rl, rv = inputs.COEXISTENCE[("guo", -5.3, 1.0)]
+    rho = inputs.ligament_density(20, 20, 24, 5.0, 0.1, rl, rv)
+    _, r_ref, u_ref, _ = oracle_run(rho, 30, G=-5.3, tau=0.7, coll="mrt", s=o.mrt_rates(0.7))
+    _, r, u = gpu_run(rho, 30, "f64", coll="mrt", tau=0.7, G=-5.3)
+    assert np.abs(r - r_ref).max() <= 1e-12
+    assert np.abs(u - u_ref).max() <= 1e-12
+
+
+@pytest.mark.parametrize("coll", ["srt", "mrt"])
+def test_one_step_populations_on_a_rough_field(coll):
+    """Every population after one step from a random two-phase density
+    (catches a wrong streaming direction or velocity order)."""
+    rho = inputs.random_density(35, 10, 9, seed=4)
+    tau = 0.9
+    s = o.mrt_rates(tau) if coll == "mrt" else None
+    f_ref, _, _, _ = oracle_run(rho, 1, tau=tau, coll=coll, s=s)
+    f64, _, _ = gpu_run(rho, 1, "f64", coll=coll, tau=tau)
+    assert np.abs(to_ref_order(f64) - f_ref).max() <= 1e-13
+    f32, _, _ = gpu_run(rho, 1, "f32", coll=coll, tau=tau)
+    assert np.abs(to_ref_order(f32) - f_ref).max() <= 2e-6
+
+
+@pytest.mark.parametrize("coll", ["srt", "mrt"])
+def test_tiling_and_chunking_do_not_change_a_bit(coll):
+    rho = inputs.noisy_ligament_density(40, 12, 23, 3.0, 0.1, RL, RV, 1e-3, seed=2)
+    ref = None
+    for tile_y in (4, 8, 16):
+        for zchunk in (1, 5, 23):
+            f, _, _ = gpu_run(rho, 10, "f64", coll=coll, tau=0.8, tile_y=tile_y, zchunk=zchunk)
+            if ref is None:
+                ref = f
+            assert np.array_equal(f, ref), (tile_y, zchunk)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 32), (1, 1, 1), (5, 1, 1), (1, 7, 3), (2, 3, 2), (33, 1, 2)])
+def test_degenerate_boxes(shape):
+    """Boxes with size-1 and size-2 axes, and smaller than a tile."""
+    nx, ny, nz = shape
+    rho = inputs.random_density(nx, ny, nz, seed=9, lo=0.3, hi=1.9)
+    for coll in ("srt", "mrt"):
+        _, r_ref, u_ref, _ = oracle_run(rho, 20, tau=0.9, coll=coll,
+                                        s=o.mrt_rates(0.9) if coll == "mrt" else None)
+        _, r, u = gpu_run(rho, 20, "f64", coll=coll, tau=0.9)
+        assert np.abs(r - r_ref).max() <= 1e-12, coll
+        assert np.abs(u - u_ref).max() <= 1e-12, coll
+
+
+def test_zero_steps_is_identity_and_counter():
+    rho = inputs.random_density(8, 8, 8, seed=1)
+    with lbm.Lattice(8, 8, 8, storage="f64") as L:
+        L.set_density(rho)
+        L.step(0)
+        r, u = L.moments()
+        assert L.time == 0
+        assert np.abs(r - rho).max() <= 1e-15
+        with pytest.raises(lbm.LbmError):
+            L.step(-1)
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-14), ("f32", 1e-6)])
+def test_ligament_initial_state_kernel(storage, tol):
+    nx, ny, nz = 24, 20, 30
+    want = inputs.ligament_density(nx, ny, nz, 5.0, 0.05, RL, RV)
+    with lbm.Lattice(nx, ny, nz, storage=storage) as L:
+        L.init_ligament(5.0, 0.05, RL, RV)
+        r, u = L.moments()
+    assert np.abs(r - want).max() <= tol * 3
+    assert np.abs(u).max() <= tol
+
+
+def test_diagnostics_match_the_reference():
+    rho0 = inputs.noisy_ligament_density(24, 24, 40, 6.0, 0.1, RL, RV, 1e-3, seed=3)
+    f_ref, r_ref, _, _ = oracle_run(rho0, 50)
+    with lbm.Lattice(24, 24, 40, storage="f64") as L:
+        L.set_density(rho0)
+        L.step(50)
+        d = L.diag(RL, RV)
+    area, mx = o.slice_diagnostics(r_ref, RL, RV)
+    assert abs(d["mass"] - r_ref.sum()) <= 1e-12 * r_ref.sum()
+    assert np.abs(d["mom"] - o.momentum(f_ref).sum(axis=(1, 2, 3))).max() <= 1e-12 * r_ref.sum()
+    assert np.abs(d["area_z"] - area).max() <= 1e-10
+    assert np.abs(d["maxrho_z"] - mx).max() <= 1e-12
+
+
+def test_fp64_conserves_mass_and_momentum_over_1000_steps():
+    rho0 = inputs.noisy_ligament_density(32, 32, 64, 8.0, 0.05, RL, RV, 1e-3, seed=7)
+    with lbm.Lattice(32, 32, 64, storage="f64") as L:
+        L.set_density(rho0)
+        d0 = L.diag(RL, RV)
+        L.step(1000)
+        d1 = L.diag(RL, RV)
+    assert abs(d1["mass"] - d0["mass"]) <= 1e-13 * d0["mass"]
+    assert np.abs(d1["mom"] - d0["mom"]).max() <= 1e-13 * d0["mass"]
+
+
+def test_nonfinite_state_is_reported():
+    rho = inputs.random_density(8, 8, 8, seed=5)
+    rho[3, 4, 5] = float("nan")
+    with lbm.Lattice(8, 8, 8, storage="f32") as L:
+        L.set_density(rho)
+        d = L.diag(2.0, 0.1, raise_nonfinite=False)
+        assert d["status"] == lbm.LBM_ENONFINITE
+        with pytest.raises(lbm.LbmError, match="LBM_ENONFINITE"):
+            L.diag(2.0, 0.1)
+
+
+# ---------------------------------------------------------------- full size
+def _patch(field, z, y, x, r):
+    """Periodic (2r+1)^3 patch of a (..., nz, ny, nx) array around (x, y, z)."""
+    nz, ny, nx = field.shape[-3:]
+    zi = np.arange(z - r, z + r + 1) % nz
+    yi = np.arange(y - r, y + r + 1) % ny
+    xi = np.arange(x - r, x + r + 1) % nx
+    if isinstance(field, torch.Tensor):
+        zi, yi, xi = (torch.as_tensor(v, device=field.device) for v in (zi, yi, xi))
+    return field[..., zi[:, None, None], yi[None, :, None], xi[None, None, :]]
+
+
+@pytest.mark.parametrize("coll", ["srt", "mrt"])
+def test_full_size_sampled_cells_match_the_reference(coll):
+    """256 x 256 x 575 (the R0 = 64, kR0 = 0.7 ligament) in FP32 with the
+    launch configuration the benchmark uses.  After 3 steps the state at 24
+    sampled sites (box corners, faces, the interface and random cells) is
+    read back; one more GPU step is compared, on the centre 3x3x3 of each
+    7x7x7 periodic patch, with the reference step applied to the same patch
+    (exact there: a cell's update reads rho within 2 cells)."""
+    nx, ny, nz = inputs.ligament_box(64, 0.7)
+    assert (nx, ny, nz) == (256, 256, 575)
+    rl, rv = (RL, RV) if coll == "srt" else (RLG, RVG)
+    rng = np.random.default_rng(0)
+    sites = [(0, 0, 0), (nx - 1, ny - 1, nz - 1), (0, ny - 1, 287), (nx - 1, 0, 1), (128, 128, 0),
+             (128, 128, nz - 1), (127 + 64, 128, 10), (128, 127 - 64, 300), (31, 32, 33), (32, 31, 574)]
+    sites += [tuple(int(v) for v in (rng.integers(nx), rng.integers(ny), rng.integers(nz))) for _ in range(14)]
+    with lbm.Lattice(nx, ny, nz, collision=coll, tau=1.0, storage="f32") as L:
+        L.init_ligament(64.0, 0.05, rl, rv)
+        L.step(3)
+        buf = torch.empty((19, nz, ny, nx), dtype=torch.float64, device="cuda")
+        L.get_populations(buf)
+        before = [_patch(buf, z, y, x, 3).cpu().numpy() for (x, y, z) in sites]
+        L.step(1)
+        L.get_populations(buf)
+        after = [_patch(buf, z, y, x, 1).cpu().numpy() for (x, y, z) in sites]
+        del buf
+    p = o.Params(G=G, tau=1.0, collision=coll)
+    for fb, fa in zip(before, after):
+        got = o.step(to_ref_order(fb), p)[:, 2:5, 2:5, 2:5]
+        assert np.abs(to_ref_order(fa) - got).max() <= 2e-6

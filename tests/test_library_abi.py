@@ -1,0 +1,84 @@
+"""The C-ABI library builds, loads and exports every symbol its header
+declares; host-side validation and tables work without a GPU.  CPU only: no
+call here launches a kernel."""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import lbm_oracle as o
+from paper_1905_09554_gb300 import lbm
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return lbm.load()
+
+
+def test_header_declares_the_boundary():
+    names = lbm.header_functions()
+    for required in ("lbm_create", "lbm_init_ligament", "lbm_step", "lbm_moments", "lbm_destroy",
+                     "lbm_diag", "lbm_set_density", "lbm_get_populations", "lbm_velocities"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in lbm.header_functions():
+        assert hasattr(lib, name), name
+        assert name in lbm._SIGNATURES, f"binding lacks {name}"
+
+
+def test_params_layout_matches(lib):
+    assert lib.lbm_params_sizeof() == ctypes.sizeof(lbm.lbm_params)
+
+
+def test_defaults(lib):
+    p = lbm.lbm_params_default()
+    assert (p.nx, p.ny, p.nz) == (32, 32, 32)
+    assert p.G == -5.5 and p.tau == 1.0 and p.storage == lbm.LBM_F32 and p.rho0 == 1.0
+
+
+def test_library_lattice_is_d3q19_with_textbook_weights(lib):
+    """The library's own velocity table is the same set as the reference's,
+    with the same weight per velocity (order may differ)."""
+    c, w = lbm.lbm_velocities()
+    lib_map = {tuple(v): wi for v, wi in zip(c, w)}
+    ref_map = {tuple(v): wi for v, wi in zip(o.C, o.W)}
+    assert lib_map.keys() == ref_map.keys()
+    for k in ref_map:
+        assert lib_map[k] == pytest.approx(ref_map[k], abs=1e-17)
+    # opposite pairs sit next to each other (1,2), (3,4), ...
+    for a in range(1, 19, 2):
+        assert tuple(-c[a]) == tuple(c[a + 1])
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("nx", 0, "box sizes"), ("tau", 0.5, "tau"), ("collision", 7, "collision"),
+    ("storage", 9, "storage"), ("rho0", -1.0, "rho0"), ("tile_y", 5, "tile_y"),
+    ("lattice", 1, "D3Q19"), ("zchunk", -2, "zchunk"),
+])
+def test_create_rejects_bad_parameters_without_touching_the_gpu(lib, field, value, msg):
+    p = lbm.lbm_params_default()
+    setattr(p, field, value)
+    st, ctx = lbm.lbm_create(p)
+    assert st == lbm.LBM_EINVAL and not ctx.value
+    assert msg in lbm.lbm_last_error(None)
+
+
+def test_create_rejects_bad_mrt_rates(lib):
+    p = lbm.lbm_params_default()
+    p.collision = lbm.LBM_MRT_GUO
+    p.has_rates = 1
+    for k in range(19):
+        p.s[k] = 1.0
+    p.s[9] = 2.5
+    st, _ = lbm.lbm_create(p)
+    assert st == lbm.LBM_EINVAL and "rates" in lbm.lbm_last_error(None)
+
+
+def test_null_context_calls_fail_cleanly(lib):
+    assert lib.lbm_step(None, 1) == lbm.LBM_EINVAL
+    assert lib.lbm_init_ligament(None, 8.0, 0.05, 1, 2.0, 2.3, 0.1) == lbm.LBM_EINVAL
+    assert lib.lbm_time(None) == -1
+    lib.lbm_destroy(None)
