@@ -52,6 +52,7 @@ def parse_args():
     ap.add_argument("--kR0", type=float, default=0.7)
     ap.add_argument("--zchunk", type=int, default=0)
     ap.add_argument("--tile-y", type=int, default=0)
+    ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 register-staged, 2 cp.async-staged")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -111,7 +112,7 @@ class ClockSampler:
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
@@ -205,8 +206,9 @@ def run_ours(args):
     nx, ny, nz = w["nx"], w["ny"], w["nz"]
     ncell = nx * ny * nz
     L = lbm.Lattice(nx, ny, nz, G=-5.5, tau=1.0, collision=args.collision, storage=args.storage,
-                    zchunk=args.zchunk, tile_y=args.tile_y)
+                    zchunk=args.zchunk, tile_y=args.tile_y, kernel=args.kernel)
     L.init_ligament(args.R0, 0.05, w["rho_l"], w["rho_v"])
+    L_info = L.kernel_config()
     stream = torch.cuda.current_stream()
     d0 = L.diag(w["rho_l"], w["rho_v"])
     L.step(args.warmup)
@@ -302,6 +304,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
         "config": {"workload": w["name"], "cells": ncell, "collision": args.collision,
                    "storage": args.storage, "parallelism": f"replicas x{world}",
+                   "kernel": L_info["kernel"], "zchunk": L_info["zchunk"], "tile_y": L_info["tile_y"],
+                   "grid": L_info["grid"],
                    "l2": "inputs larger than L2 (two population copies of "
                          f"{19 * BYTES_PER_POP[args.storage] * ncell / 1e9:.2f} GB each)",
                    "mass_rel_drift": mass_drift},

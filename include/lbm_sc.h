@@ -78,6 +78,9 @@ typedef struct {
                              allocates (and frees them in lbm_destroy).            */
     int zchunk;           /* step kernel: z planes per thread block; 0 = auto       */
     int tile_y;           /* step kernel: tile height (4, 8 or 16); 0 = auto        */
+    int kernel;           /* step kernel variant: 0 = auto, 1 = register-staged,
+                             2 = cp.async-staged persistent, 3 = pipelined
+                             persistent (2 and 3: FP64/FP32 storage only)           */
 } lbm_params;
 
 /* Fill *p with defaults: D3Q19, 32^3, G = -5.5, SRT tau = 1, psi exp, rho0 = 1,
@@ -151,6 +154,12 @@ lbm_status lbm_set_stream(lbm_ctx *ctx, void *stream);
 
 /* Bytes of device memory the context allocated itself. */
 long long lbm_device_bytes(const lbm_ctx *ctx);
+
+/* Launch configuration the context chose for the step kernel: variant
+ * (1 register-staged, 2 cp.async-staged, 3 pipelined), tile height, z planes
+ * per work item and grid size (blocks).  Any pointer may be NULL. */
+lbm_status lbm_kernel_config(const lbm_ctx *ctx, int *kernel, int *tile_y,
+                             int *zchunk, int *grid);
 
 /* sizeof(lbm_params) in this build, so that bindings can check their layout. */
 long long lbm_params_sizeof(void);

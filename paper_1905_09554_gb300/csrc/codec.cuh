@@ -25,6 +25,8 @@ struct CodecF64 {
     using R = double;
     static constexpr int kStorage = 0;
     template <int q>
+    __device__ __forceinline__ static R decode(S v, const DevParams&) { return v; }
+    template <int q>
     __device__ __forceinline__ static R load(const S* p, const DevParams&) { return __ldg(p); }
     template <int q>
     __device__ __forceinline__ static void store(S* p, R v, const DevParams&) { *p = v; }
@@ -34,6 +36,8 @@ struct CodecF32 {
     using S = float;
     using R = float;
     static constexpr int kStorage = 1;
+    template <int q>
+    __device__ __forceinline__ static R decode(S v, const DevParams&) { return v; }
     template <int q>
     __device__ __forceinline__ static R load(const S* p, const DevParams&) { return __ldg(p); }
     template <int q>
@@ -45,9 +49,11 @@ struct CodecF16Dev {
     using R = float;
     static constexpr int kStorage = 2;
     template <int q>
-    __device__ __forceinline__ static R load(const S* p, const DevParams& d) {
-        return float(wq(q)) * d.rho_ref + __half2float(__ldg(p)) * d.inv_scale;
+    __device__ __forceinline__ static R decode(S v, const DevParams& d) {
+        return float(wq(q)) * d.rho_ref + __half2float(v) * d.inv_scale;
     }
+    template <int q>
+    __device__ __forceinline__ static R load(const S* p, const DevParams& d) { return decode<q>(__ldg(p), d); }
     template <int q>
     __device__ __forceinline__ static void store(S* p, R v, const DevParams& d) {
         *p = __float2half_rn((v - float(wq(q)) * d.rho_ref) * d.scale);
@@ -59,9 +65,11 @@ struct CodecBF16Dev {
     using R = float;
     static constexpr int kStorage = 3;
     template <int q>
-    __device__ __forceinline__ static R load(const S* p, const DevParams& d) {
-        return float(wq(q)) * d.rho_ref + __bfloat162float(__ldg(p)) * d.inv_scale;
+    __device__ __forceinline__ static R decode(S v, const DevParams& d) {
+        return float(wq(q)) * d.rho_ref + __bfloat162float(v) * d.inv_scale;
     }
+    template <int q>
+    __device__ __forceinline__ static R load(const S* p, const DevParams& d) { return decode<q>(__ldg(p), d); }
     template <int q>
     __device__ __forceinline__ static void store(S* p, R v, const DevParams& d) {
         *p = __float2bfloat16_rn((v - float(wq(q)) * d.rho_ref) * d.scale);

@@ -35,6 +35,8 @@ struct lbm_ctx {
     long long own_bytes = 0;
     StepArgs args{};
     int zchunk = 0, tile_y = 8;
+    int kernel = 1;                   // 1 register-staged, 2 cp.async persistent
+    int grid = 0;                     // persistent grid size (kernel 2)
     char err[512] = {0};
 
     lbm_status fail(lbm_status s, const char* fmt, ...) {
@@ -242,10 +244,75 @@ template <class Codec, int COLL, int TY>
 cudaError_t launch_step_t(const lbm_ctx* c, const void* src, void* dst) {
     constexpr int TX = 32;
     const StepArgs& a = c->args;
+    if constexpr (sizeof(typename Codec::S) >= 4) {
+        if (c->kernel == 3) {
+            sc_step_pipe_kernel<Codec, COLL, TX, TY><<<c->grid, TX * TY, PipeLayout<Codec, TX, TY>::bytes, c->stream>>>(
+                static_cast<const typename Codec::S*>(src), static_cast<typename Codec::S*>(dst), a);
+            return cudaGetLastError();
+        }
+    }
+    if constexpr (sizeof(typename Codec::S) >= 4 && (TY <= 8 || sizeof(typename Codec::S) == 4)) {
+        if (c->kernel == 2) {
+            sc_step_async_kernel<Codec, COLL, TX, TY><<<c->grid, TX * TY, AsyncLayout<Codec, TX, TY>::bytes, c->stream>>>(
+                static_cast<const typename Codec::S*>(src), static_cast<typename Codec::S*>(dst), a);
+            return cudaGetLastError();
+        }
+    }
     dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + a.zchunk - 1) / a.zchunk);
     sc_step_kernel<Codec, COLL, TX, TY><<<grid, TX * TY, 0, c->stream>>>(
         static_cast<const typename Codec::S*>(src), static_cast<typename Codec::S*>(dst), a);
     return cudaGetLastError();
+}
+
+// Prepare the cp.async kernel: opt in to its shared memory and size the
+// persistent grid from the occupancy calculator.  Returns 0 if the variant
+// cannot run for this storage/tile.
+template <class Codec, int COLL, int TY>
+int prepare_async_t(lbm_ctx* c) {
+    constexpr int TX = 32;
+    if constexpr (sizeof(typename Codec::S) >= 4) {
+        if (c->kernel == 3) {
+            using Lay = PipeLayout<Codec, TX, TY>;
+            auto kern = sc_step_pipe_kernel<Codec, COLL, TX, TY>;
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes) !=
+                cudaSuccess)
+                return 0;
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, Lay::bytes) != cudaSuccess)
+                return 0;
+            return per_sm;
+        }
+    }
+    if constexpr (sizeof(typename Codec::S) >= 4 && (TY <= 8 || sizeof(typename Codec::S) == 4)) {
+        using Lay = AsyncLayout<Codec, TX, TY>;
+        auto kern = sc_step_async_kernel<Codec, COLL, TX, TY>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes) != cudaSuccess)
+            return 0;
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, Lay::bytes) != cudaSuccess ||
+            per_sm < 1)
+            return 0;
+        return per_sm;
+    }
+    return 0;
+}
+
+template <class Codec, int COLL>
+int prepare_async_c(lbm_ctx* c) {
+    switch (c->tile_y) {
+        case 4: return prepare_async_t<Codec, COLL, 4>(c);
+        case 16: return prepare_async_t<Codec, COLL, 16>(c);
+        default: return prepare_async_t<Codec, COLL, 8>(c);
+    }
+}
+
+int prepare_async(lbm_ctx* c) {
+    const bool mrt = c->p.collision == LBM_MRT_GUO;
+    switch (c->p.storage) {
+        case LBM_F64: return mrt ? prepare_async_c<CodecF64, COLL_MRT>(c) : prepare_async_c<CodecF64, COLL_SRT>(c);
+        case LBM_F32: return mrt ? prepare_async_c<CodecF32, COLL_MRT>(c) : prepare_async_c<CodecF32, COLL_SRT>(c);
+        default: return 0;
+    }
 }
 
 template <class Codec, int COLL>
@@ -448,9 +515,49 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     a.dev.rho_ref = float(p->rho_ref);
     a.dev.scale = float(p->dev_scale);
     a.dev.inv_scale = float(1.0 / p->dev_scale);
-    c->tile_y = p->tile_y ? p->tile_y : 8;
-    c->zchunk = p->zchunk ? (p->zchunk < p->nz ? p->zchunk : p->nz) : auto_zchunk(c);
+    // Auto launch shape (measured on GB300 at 256x256x575): FP32 SRT runs the
+    // pipelined kernel on 32x16 tiles; MRT and the other storage types run the
+    // register-staged kernel on 32x4 tiles.
+    const bool pipe_default = p->storage == LBM_F32 && p->collision == LBM_SRT_SHIFT;
+    c->tile_y = p->tile_y ? p->tile_y : ((p->kernel == 3 || (p->kernel == 0 && pipe_default)) ? 16 : 4);
+    if (p->kernel < 0 || p->kernel > 3) {
+        snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel must be 0, 1, 2 or 3");
+        lbm_destroy(c);
+        return LBM_EINVAL;
+    }
+    c->kernel = 1;
+    if (p->kernel != 1 && !(p->kernel == 0 && !pipe_default)) {
+        c->kernel = p->kernel == 0 ? 3 : p->kernel;
+        const int per_sm = prepare_async(c);
+        if (per_sm > 0) {
+            c->grid = per_sm * c->num_sms;
+        } else if (p->kernel >= 2) {
+            snprintf(g_create_err, sizeof(g_create_err),
+                     "lbm_create: kernel %d needs FP64/FP32 storage (kernel 2 with FP64: tile_y <= 8)", p->kernel);
+            lbm_destroy(c);
+            return LBM_EINVAL;
+        } else {
+            c->kernel = 1;
+        }
+    }
+    const int tiles_x = (p->nx + 31) / 32, tiles_y = (p->ny + c->tile_y - 1) / c->tile_y;
+    if (p->zchunk) {
+        c->zchunk = p->zchunk < p->nz ? p->zchunk : p->nz;
+    } else if (c->kernel >= 2) {
+        // about 8 work items per block of the persistent grid, chunks >= 8 planes
+        const long long tiles = (long long)tiles_x * tiles_y;
+        long long chunks = (8LL * c->grid + tiles - 1) / tiles;
+        long long zc = (p->nz + chunks - 1) / chunks;
+        if (zc < 8) zc = 8;
+        c->zchunk = int(zc < p->nz ? zc : p->nz);
+    } else {
+        c->zchunk = auto_zchunk(c);
+    }
     a.zchunk = c->zchunk;
+    a.tiles_x = tiles_x;
+    a.n_tiles = tiles_x * tiles_y;
+    a.n_items = a.n_tiles * ((p->nz + c->zchunk - 1) / c->zchunk);
+    if (c->kernel >= 2 && c->grid > a.n_items) c->grid = a.n_items;
 
     e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -483,6 +590,22 @@ lbm_status lbm_set_stream(lbm_ctx* c, void* stream) {
 long lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
 
 long long lbm_device_bytes(const lbm_ctx* c) { return c ? c->own_bytes : 0; }
+
+lbm_status lbm_kernel_config(const lbm_ctx* c, int* kernel, int* tile_y, int* zchunk, int* grid) {
+    if (!c) return LBM_EINVAL;
+    if (kernel) *kernel = c->kernel;
+    if (tile_y) *tile_y = c->tile_y;
+    if (zchunk) *zchunk = c->zchunk;
+    if (grid) {
+        if (c->kernel >= 2) {
+            *grid = c->grid;
+        } else {
+            const StepArgs& a = c->args;
+            *grid = ((a.nx + 31) / 32) * ((a.ny + c->tile_y - 1) / c->tile_y) * ((a.nz + a.zchunk - 1) / a.zchunk);
+        }
+    }
+    return LBM_OK;
+}
 
 long long lbm_params_sizeof(void) { return (long long)sizeof(lbm_params); }
 

@@ -30,7 +30,9 @@ enum { COLL_SRT = 0, COLL_MRT = 1 };
 
 struct StepArgs {
     int nx, ny, nz;
-    int zchunk;           // planes per block along z
+    int zchunk;           // planes per block (work item) along z
+    int tiles_x, n_tiles; // xy tiles of the persistent kernel
+    int n_items;          // n_tiles * number of z chunks
     long long n;          // cells = nx*ny*nz (population stride)
     double G;             // interaction strength G0
     double tau, omega;    // SRT relaxation time and 1/tau
@@ -170,6 +172,39 @@ __device__ __forceinline__ typename Codec::R cell_density(const typename Codec::
     return r;
 }
 
+// Force from the psi ring (planes z-1, z, z+1 of the tile + ring), collision
+// of the cell's populations fc, and push to x + c_a in `dst`.
+template <class Codec, int COLL, int PX>
+__device__ __forceinline__ void update_cell(typename Codec::R (&fc)[Q], const typename Codec::R* pm,
+                                            const typename Codec::R* p0, const typename Codec::R* pp,
+                                            int slot, typename Codec::S* __restrict__ dst, long long n,
+                                            const long long (&zoff)[3], const long long (&yoff)[3],
+                                            const int (&xidx)[3], const StepArgs& a) {
+    using R = typename Codec::R;
+    const R* pl[3] = {pm, p0, pp};
+    // Eq. SC_force: F = -G psi(x) sum_a w_a psi(x + c_a) c_a.
+    R sx = R(0), sy = R(0), sz = R(0);
+    static_for<1, Q>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        const R v = pl[cz(q) + 1][slot + cx(q) + cy(q) * PX];
+        if constexpr (cx(q) != 0) sx += R(wq(q) * cx(q)) * v;
+        if constexpr (cy(q) != 0) sy += R(wq(q) * cy(q)) * v;
+        if constexpr (cz(q) != 0) sz += R(wq(q) * cz(q)) * v;
+    });
+    const R gpsi = -R(a.G) * p0[slot];
+    const R Fx = gpsi * sx, Fy = gpsi * sy, Fz = gpsi * sz;
+
+    if constexpr (COLL == COLL_SRT) collide_srt<R>(fc, Fx, Fy, Fz, R(a.tau), R(a.omega));
+    else collide_mrt<R>(fc, Fx, Fy, Fz, a.s);
+
+    // Eq. LBE streaming: f_a(x + c_a, t + 1) = f*_a(x, t).
+    static_for<0, Q>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        const long long idx = zoff[cz(q) + 1] + yoff[cy(q) + 1] + xidx[cx(q) + 1];
+        Codec::template store<q>(dst + q * n + idx, fc[q], a.dev);
+    });
+}
+
 template <class Codec, int COLL, int TX, int TY>
 __global__ void __launch_bounds__(TX * TY)
 sc_step_kernel(const typename Codec::S* __restrict__ src, typename Codec::S* __restrict__ dst,
@@ -215,7 +250,6 @@ sc_step_kernel(const typename Codec::S* __restrict__ src, typename Codec::S* __r
     const int xidx[3] = {xm, gx, xp};
 
     const R rho0 = R(a.rho0), inv_rho0 = R(a.inv_rho0);
-    const R G = R(a.G), tau = R(a.tau), omega = R(a.omega);
     const DevParams dev = a.dev;
 
     auto slot_of = [&](int z) { return (z - zs + 1) & (NSLOT - 1); };
@@ -265,36 +299,328 @@ sc_step_kernel(const typename Codec::S* __restrict__ src, typename Codec::S* __r
         __syncthreads();
 
         if (active) {
-            const R* pl[3] = {psi_s[slot_of(z - 1)], psi_s[slot_of(z)], psi_s[zp_slot]};
-            // Eq. SC_force: F = -G psi(x) sum_a w_a psi(x + c_a) c_a.
-            R sx = R(0), sy = R(0), sz = R(0);
-            static_for<1, Q>([&](auto qc) {
-                constexpr int q = decltype(qc)::value;
-                const R v = pl[cz(q) + 1][my_slot + cx(q) + cy(q) * PX];
-                if constexpr (cx(q) != 0) sx += R(wq(q) * cx(q)) * v;
-                if constexpr (cy(q) != 0) sy += R(wq(q) * cy(q)) * v;
-                if constexpr (cz(q) != 0) sz += R(wq(q) * cz(q)) * v;
-            });
-            const R gpsi = -G * pl[1][my_slot];
-            const R Fx = gpsi * sx, Fy = gpsi * sy, Fz = gpsi * sz;
-
-            if constexpr (COLL == COLL_SRT) collide_srt<R>(fc, Fx, Fy, Fz, tau, omega);
-            else collide_mrt<R>(fc, Fx, Fy, Fz, a.s);
-
-            // Eq. LBE streaming: f_a(x + c_a, t + 1) = f*_a(x, t).
             const int zm = (z == 0) ? nz - 1 : z - 1;
             const long long zoff[3] = {(long long)zm * plane, (long long)z * plane, (long long)zn * plane};
-            static_for<0, Q>([&](auto qc) {
-                constexpr int q = decltype(qc)::value;
-                const long long idx = zoff[cz(q) + 1] + yoff[cy(q) + 1] + xidx[cx(q) + 1];
-                Codec::template store<q>(dst + q * n + idx, fc[q], dev);
-            });
+            update_cell<Codec, COLL, PX>(fc, psi_s[slot_of(z - 1)], psi_s[slot_of(z)], psi_s[zp_slot], my_slot,
+                                         dst, n, zoff, yoff, xidx, a);
         }
         static_for<0, Q>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
             fc[q] = fn[q];
         });
     }
+}
+
+
+// ----------------------------------------------------------------------------
+// Asynchronous-copy variant (FP32 / FP64 storage).
+//
+// Same arithmetic as sc_step_kernel, but the populations of each plane (the
+// tile's cells and its one-cell ring) are fetched with cp.async into a
+// three-stage shared-memory pipeline two planes ahead of the collision, so
+// the loads in flight per SM no longer depend on registers.  Every thread
+// reads back only the stage slots it copied itself, so the stages need no
+// barrier; the psi ring keeps its single barrier per plane.  The grid is
+// persistent: each block walks work items (xy tile, z chunk) in a fixed
+// round-robin order.
+// ----------------------------------------------------------------------------
+namespace async_copy {
+__device__ __forceinline__ void commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+template <int BYTES>
+__device__ __forceinline__ void copy(void* smem, const void* gmem) {
+    static_assert(BYTES == 4 || BYTES == 8, "cp.async element size");
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+}
+}  // namespace async_copy
+
+template <class Codec, int TX, int TY>
+struct AsyncLayout {
+    using S = typename Codec::S;
+    using R = typename Codec::R;
+    static constexpr int NT = TX * TY;
+    static constexpr int NHALO = 2 * (TX + 2) + 2 * TY;
+    static constexpr int PX = TX + 2;
+    static constexpr int PLANE = PX * (TY + 2);
+    static constexpr int NSTAGE = 3;
+    static constexpr int NSLOT = 4;
+    static constexpr int SLOTS = NT + NHALO;  // stage slots per population
+    static constexpr size_t stage_bytes = sizeof(S) * Q * SLOTS;
+    static constexpr size_t bytes = NSTAGE * stage_bytes + sizeof(R) * NSLOT * PLANE;
+};
+
+template <class Codec, int COLL, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY)
+sc_step_async_kernel(const typename Codec::S* __restrict__ src, typename Codec::S* __restrict__ dst,
+                     const StepArgs a) {
+    using R = typename Codec::R;
+    using S = typename Codec::S;
+    using L = AsyncLayout<Codec, TX, TY>;
+    constexpr int PX = L::PX, PLANE = L::PLANE, NT = L::NT, SLOTS = L::SLOTS;
+    static_assert(L::NHALO <= NT, "tile too small for its halo ring");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* stage = reinterpret_cast<S*>(smem_raw);
+    R* ring = reinterpret_cast<R*>(smem_raw + L::NSTAGE * L::stage_bytes);
+
+    const int tid = threadIdx.x;
+    const int lx = tid % TX, ly = tid / TX;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const long long n = a.n;
+    const long long plane = (long long)nx * ny;
+    const R rho0 = R(a.rho0), inv_rho0 = R(a.inv_rho0);
+    const DevParams dev = a.dev;
+    const int my_slot = (ly + 1) * PX + (lx + 1);
+
+    // Ring cell of this thread, as tile-relative coordinates (fixed per thread).
+    int hx = 0, hy = 0, h_slot = -1;
+    if (tid < L::NHALO) {
+        if (tid < PX) { hx = tid - 1; hy = -1; }
+        else if (tid < 2 * PX) { hx = tid - PX - 1; hy = TY; }
+        else { const int k = tid - 2 * PX; hx = (k < TY) ? -1 : TX; hy = (k < TY) ? k : k - TY; }
+        h_slot = (hy + 1) * PX + (hx + 1);
+    }
+
+    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+        const int tile = item % a.n_tiles, chunk = item / a.n_tiles;
+        const int x0 = (tile % a.tiles_x) * TX, y0 = (tile / a.tiles_x) * TY;
+        const int zs = chunk * a.zchunk;
+        const int ze = min(zs + a.zchunk, nz);
+
+        const int gx = wrap_index(x0 + lx, nx), gy = wrap_index(y0 + ly, ny);
+        const bool active = (x0 + lx < nx) && (y0 + ly < ny);
+        const long long my_xy = (long long)gy * nx + gx;
+        const long long h_xy = (h_slot >= 0) ? (long long)wrap_index(y0 + hy, ny) * nx + wrap_index(x0 + hx, nx) : 0;
+        const int xp = (gx + 1 == nx) ? 0 : gx + 1, xm = (gx == 0) ? nx - 1 : gx - 1;
+        const int yp = (gy + 1 == ny) ? 0 : gy + 1, ym = (gy == 0) ? ny - 1 : gy - 1;
+        const long long yoff[3] = {(long long)ym * nx, (long long)gy * nx, (long long)yp * nx};
+        const int xidx[3] = {xm, gx, xp};
+
+        auto stage_of = [&](int z) { return (z - zs + 1) % L::NSTAGE; };
+        auto slot_of = [&](int z) { return (z - zs + 1) & (L::NSLOT - 1); };
+        // Copy plane z (periodic) of this thread's cell and ring cell.
+        auto issue = [&](int z) {
+            const int zw = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+            const S* base = src + (long long)zw * plane;
+            S* st = stage + stage_of(z) * (Q * SLOTS);
+            static_for<0, Q>([&](auto qc) {
+                constexpr int q = decltype(qc)::value;
+                async_copy::copy<sizeof(S)>(st + q * SLOTS + tid, base + q * n + my_xy);
+            });
+            if (h_slot >= 0) {
+                static_for<0, Q>([&](auto qc) {
+                    constexpr int q = decltype(qc)::value;
+                    async_copy::copy<sizeof(S)>(st + q * SLOTS + NT + tid, base + q * n + h_xy);
+                });
+            }
+            async_copy::commit();
+        };
+        auto psi_from_stage = [&](int z) {
+            const S* st = stage + stage_of(z) * (Q * SLOTS);
+            R r = R(0);
+            static_for<0, Q>([&](auto qc) {
+                constexpr int q = decltype(qc)::value;
+                r += Codec::template decode<q>(st[q * SLOTS + tid], dev);
+            });
+            ring[slot_of(z) * PLANE + my_slot] = psi_of<R>(r, rho0, inv_rho0);
+            if (h_slot >= 0) {
+                R rh = R(0);
+                static_for<0, Q>([&](auto qc) {
+                    constexpr int q = decltype(qc)::value;
+                    rh += Codec::template decode<q>(st[q * SLOTS + NT + tid], dev);
+                });
+                ring[slot_of(z) * PLANE + h_slot] = psi_of<R>(rh, rho0, inv_rho0);
+            }
+        };
+
+        __syncthreads();  // the previous item's readers of the psi ring are done
+        issue(zs - 1);
+        issue(zs);
+        issue(zs + 1);
+        async_copy::wait<2>();
+        psi_from_stage(zs - 1);
+        async_copy::wait<1>();
+        psi_from_stage(zs);
+
+        for (int z = zs; z < ze; ++z) {
+            if (z + 2 <= ze) issue(z + 2);
+            else async_copy::commit();
+            async_copy::wait<1>();
+            psi_from_stage(z + 1);
+            __syncthreads();
+            if (active) {
+                const S* st = stage + stage_of(z) * (Q * SLOTS);
+                R fc[Q];
+                static_for<0, Q>([&](auto qc) {
+                    constexpr int q = decltype(qc)::value;
+                    fc[q] = Codec::template decode<q>(st[q * SLOTS + tid], dev);
+                });
+                const int zm = (z == 0) ? nz - 1 : z - 1;
+                const int zn = (z + 1 == nz) ? 0 : z + 1;
+                const long long zoff[3] = {(long long)zm * plane, (long long)z * plane, (long long)zn * plane};
+                update_cell<Codec, COLL, PX>(fc, ring + slot_of(z - 1) * PLANE, ring + slot_of(z) * PLANE,
+                                             ring + slot_of(z + 1) * PLANE, my_slot, dst, n, zoff, yoff, xidx, a);
+            }
+        }
+    }
+    async_copy::wait<0>();
+}
+
+// ----------------------------------------------------------------------------
+// Pipelined variant (FP32 / FP64 storage).
+//
+// The register-staged kernel waits for each plane's loads right after issuing
+// them.  Here the loads of plane z+2 are issued before the collision of
+// plane z and consumed after it, so one plane of loads per thread is always
+// in flight while the block computes.  The ring cells' populations (needed
+// only for psi) go through a three-stage cp.async buffer two planes ahead,
+// so ring loads never stall the block's barrier.  Persistent grid over
+// (xy tile, z chunk) work items as in sc_step_async_kernel.
+// ----------------------------------------------------------------------------
+template <class Codec, int TX, int TY>
+struct PipeLayout {
+    using S = typename Codec::S;
+    using R = typename Codec::R;
+    static constexpr int NT = TX * TY;
+    static constexpr int NHALO = 2 * (TX + 2) + 2 * TY;
+    static constexpr int PX = TX + 2;
+    static constexpr int PLANE = PX * (TY + 2);
+    static constexpr int NSTAGE = 3;
+    static constexpr int NSLOT = 4;
+    static constexpr size_t stage_bytes = sizeof(S) * Q * NHALO;
+    static constexpr size_t bytes = NSTAGE * stage_bytes + sizeof(R) * NSLOT * PLANE;
+};
+
+// Register budget: at most 65536 / (512 threads) = 128 registers per thread
+// so that 512 threads per SM stay resident.
+template <class Codec, int COLL, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, (TX * TY >= 512) ? 1 : 512 / (TX * TY))
+sc_step_pipe_kernel(const typename Codec::S* __restrict__ src, typename Codec::S* __restrict__ dst,
+                    const StepArgs a) {
+    using R = typename Codec::R;
+    using S = typename Codec::S;
+    using L = PipeLayout<Codec, TX, TY>;
+    constexpr int PX = L::PX, PLANE = L::PLANE, NH = L::NHALO;
+    static_assert(L::NHALO <= TX * TY, "tile too small for its halo ring");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* hstage = reinterpret_cast<S*>(smem_raw);  // [NSTAGE][Q][NHALO]
+    R* ring = reinterpret_cast<R*>(smem_raw + L::NSTAGE * L::stage_bytes);
+
+    const int tid = threadIdx.x;
+    const int lx = tid % TX, ly = tid / TX;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const long long n = a.n;
+    const long long plane = (long long)nx * ny;
+    const R rho0 = R(a.rho0), inv_rho0 = R(a.inv_rho0);
+    const DevParams dev = a.dev;
+    const int my_slot = (ly + 1) * PX + (lx + 1);
+
+    int hx = 0, hy = 0, h_slot = -1;
+    if (tid < NH) {
+        if (tid < PX) { hx = tid - 1; hy = -1; }
+        else if (tid < 2 * PX) { hx = tid - PX - 1; hy = TY; }
+        else { const int k = tid - 2 * PX; hx = (k < TY) ? -1 : TX; hy = (k < TY) ? k : k - TY; }
+        h_slot = (hy + 1) * PX + (hx + 1);
+    }
+
+    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+        const int tile = item % a.n_tiles, chunk = item / a.n_tiles;
+        const int x0 = (tile % a.tiles_x) * TX, y0 = (tile / a.tiles_x) * TY;
+        const int zs = chunk * a.zchunk;
+        const int ze = min(zs + a.zchunk, nz);
+
+        const int gx = wrap_index(x0 + lx, nx), gy = wrap_index(y0 + ly, ny);
+        const bool active = (x0 + lx < nx) && (y0 + ly < ny);
+        const long long my_xy = (long long)gy * nx + gx;
+        const long long h_xy = (h_slot >= 0) ? (long long)wrap_index(y0 + hy, ny) * nx + wrap_index(x0 + hx, nx) : 0;
+        const int xp = (gx + 1 == nx) ? 0 : gx + 1, xm = (gx == 0) ? nx - 1 : gx - 1;
+        const int yp = (gy + 1 == ny) ? 0 : gy + 1, ym = (gy == 0) ? ny - 1 : gy - 1;
+        const long long yoff[3] = {(long long)ym * nx, (long long)gy * nx, (long long)yp * nx};
+        const int xidx[3] = {xm, gx, xp};
+
+        auto wrapz = [&](int z) { return z < 0 ? z + nz : (z >= nz ? z - nz : z); };
+        auto stage_of = [&](int z) { return (z - zs + 1) % L::NSTAGE; };
+        auto slot_of = [&](int z) { return (z - zs + 1) & (L::NSLOT - 1); };
+        auto issue_halo = [&](int z) {
+            if (h_slot >= 0) {
+                const S* base = src + (long long)wrapz(z) * plane + h_xy;
+                S* st = hstage + stage_of(z) * (Q * NH);
+                static_for<0, Q>([&](auto qc) {
+                    constexpr int q = decltype(qc)::value;
+                    async_copy::copy<sizeof(S)>(st + q * NH + tid, base + q * n);
+                });
+            }
+            async_copy::commit();
+        };
+        auto halo_psi = [&](int z) {
+            if (h_slot >= 0) {
+                const S* st = hstage + stage_of(z) * (Q * NH);
+                R r = R(0);
+                static_for<0, Q>([&](auto qc) {
+                    constexpr int q = decltype(qc)::value;
+                    r += Codec::template decode<q>(st[q * NH + tid], dev);
+                });
+                ring[slot_of(z) * PLANE + h_slot] = psi_of<R>(r, rho0, inv_rho0);
+            }
+        };
+        auto load_plane = [&](R (&f)[Q], int z) {
+            const S* base = src + (long long)wrapz(z) * plane + my_xy;
+            static_for<0, Q>([&](auto qc) {
+                constexpr int q = decltype(qc)::value;
+                f[q] = Codec::template load<q>(base + q * n, dev);
+            });
+        };
+        auto own_psi = [&](const R (&f)[Q], int z) {
+            R r = R(0);
+            static_for<0, Q>([&](auto qc) {
+                constexpr int q = decltype(qc)::value;
+                r += f[q];
+            });
+            ring[slot_of(z) * PLANE + my_slot] = psi_of<R>(r, rho0, inv_rho0);
+        };
+
+        __syncthreads();  // the previous item's readers of the psi ring are done
+        issue_halo(zs - 1);
+        issue_halo(zs);
+        issue_halo(zs + 1);
+        R fc[Q], fn[Q];
+        load_plane(fc, zs - 1);
+        own_psi(fc, zs - 1);
+        load_plane(fc, zs);
+        load_plane(fn, zs + 1);
+        async_copy::wait<2>();
+        halo_psi(zs - 1);
+        async_copy::wait<1>();
+        halo_psi(zs);
+        own_psi(fc, zs);
+        own_psi(fn, zs + 1);
+
+        for (int z = zs; z < ze; ++z) {
+            const bool more = z + 2 <= ze;
+            R fl[Q];
+            if (more) load_plane(fl, z + 2);
+            if (more) issue_halo(z + 2);
+            else async_copy::commit();
+            async_copy::wait<1>();
+            halo_psi(z + 1);
+            __syncthreads();
+            if (active) {
+                const int zm = (z == 0) ? nz - 1 : z - 1;
+                const int zn = (z + 1 == nz) ? 0 : z + 1;
+                const long long zoff[3] = {(long long)zm * plane, (long long)z * plane, (long long)zn * plane};
+                update_cell<Codec, COLL, PX>(fc, ring + slot_of(z - 1) * PLANE, ring + slot_of(z) * PLANE,
+                                             ring + slot_of(z + 1) * PLANE, my_slot, dst, n, zoff, yoff, xidx, a);
+            }
+            if (more) own_psi(fl, z + 2);
+            static_for<0, Q>([&](auto qc) {
+                constexpr int q = decltype(qc)::value;
+                fc[q] = fn[q];
+                if (more) fn[q] = fl[q];
+            });
+        }
+    }
+    async_copy::wait<0>();
 }
 
 }  // namespace lbm

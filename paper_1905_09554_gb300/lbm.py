@@ -52,6 +52,7 @@ class lbm_params(ctypes.Structure):
         ("f_a", ctypes.c_void_p), ("f_b", ctypes.c_void_p),
         ("zchunk", ctypes.c_int),
         ("tile_y", ctypes.c_int),
+        ("kernel", ctypes.c_int),
     ]
 
 
@@ -75,6 +76,8 @@ _SIGNATURES = {
     "lbm_set_stream": (ctypes.c_int, [_P, _P]),
     "lbm_device_bytes": (ctypes.c_longlong, [_P]),
     "lbm_params_sizeof": (ctypes.c_longlong, []),
+    "lbm_kernel_config": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
 }
 
 _lib = None
@@ -181,6 +184,12 @@ def lbm_device_bytes(ctx):
     return load().lbm_device_bytes(ctx)
 
 
+def lbm_kernel_config(ctx):
+    v = [ctypes.c_int() for _ in range(4)]
+    st = load().lbm_kernel_config(ctx, *[ctypes.byref(x) for x in v])
+    return st, dict(zip(("kernel", "tile_y", "zchunk", "grid"), (x.value for x in v)))
+
+
 # ------------------------------------------------------------ object wrapper
 def _host_ptr(a: np.ndarray):
     return a.ctypes.data_as(_P)
@@ -198,7 +207,7 @@ class Lattice:
 
     def __init__(self, nx, ny, nz, G=-5.5, tau=1.0, collision="srt", rates=None,
                  storage="f32", rho0=1.0, rho_ref=1.0, dev_scale=1.0,
-                 torch_buffers=True, stream=None, zchunk=0, tile_y=0):
+                 torch_buffers=True, stream=None, zchunk=0, tile_y=0, kernel=0):
         lib = load()
         p = lbm_params_default()
         p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
@@ -210,7 +219,7 @@ class Lattice:
                 p.s[k] = float(v)
         p.storage = STORAGE[storage]
         p.rho_ref, p.dev_scale = float(rho_ref), float(dev_scale)
-        p.zchunk, p.tile_y = int(zchunk), int(tile_y)
+        p.zchunk, p.tile_y, p.kernel = int(zchunk), int(tile_y), int(kernel)
         self.shape = (int(nz), int(ny), int(nx))
         self.n = int(nx) * int(ny) * int(nz)
         self.storage = storage
@@ -326,3 +335,8 @@ class Lattice:
 
     def device_bytes(self):
         return lbm_device_bytes(self.ctx)
+
+    def kernel_config(self):
+        st, cfg = lbm_kernel_config(self.ctx)
+        self._check(st)
+        return cfg

@@ -124,16 +124,29 @@ def test_one_step_populations_on_a_rough_field(coll):
     assert np.abs(to_ref_order(f32) - f_ref).max() <= 2e-6
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32"])
 @pytest.mark.parametrize("coll", ["srt", "mrt"])
-def test_tiling_and_chunking_do_not_change_a_bit(coll):
+def test_kernel_variant_tiling_and_chunking_do_not_change_a_bit(coll, storage):
+    """Register-staged, cp.async-staged and pipelined kernels, every tile
+    height and z-chunk length give bit-identical states."""
     rho = inputs.noisy_ligament_density(40, 12, 23, 3.0, 0.1, RL, RV, 1e-3, seed=2)
     ref = None
-    for tile_y in (4, 8, 16):
-        for zchunk in (1, 5, 23):
-            f, _, _ = gpu_run(rho, 10, "f64", coll=coll, tau=0.8, tile_y=tile_y, zchunk=zchunk)
-            if ref is None:
-                ref = f
-            assert np.array_equal(f, ref), (tile_y, zchunk)
+    for kernel in (1, 2, 3):
+        for tile_y in (4, 8, 16):
+            if kernel == 2 and storage == "f64" and tile_y == 16:
+                continue
+            for zchunk in (1, 5, 23):
+                f, _, _ = gpu_run(rho, 10, storage, coll=coll, tau=0.8, tile_y=tile_y, zchunk=zchunk,
+                                  kernel=kernel)
+                if ref is None:
+                    ref = f
+                assert np.array_equal(f, ref), (kernel, tile_y, zchunk)
+
+
+@pytest.mark.parametrize("kernel", [2, 3])
+def test_staged_kernels_reject_16_bit_storage(kernel):
+    with pytest.raises(lbm.LbmError, match="LBM_EINVAL"):
+        lbm.Lattice(8, 8, 8, storage="f16", kernel=kernel)
 
 
 @pytest.mark.parametrize("shape", [(1, 1, 32), (1, 1, 1), (5, 1, 1), (1, 7, 3), (2, 3, 2), (33, 1, 2)])
@@ -156,20 +169,23 @@ def test_zero_steps_is_identity_and_counter():
         L.step(0)
         r, u = L.moments()
         assert L.time == 0
-        assert np.abs(r - rho).max() <= 1e-15
+        assert np.abs(r - rho).max() <= 8 * np.finfo(float).eps * rho.max()
         with pytest.raises(lbm.LbmError):
             L.step(-1)
 
 
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-14), ("f32", 1e-6)])
 def test_ligament_initial_state_kernel(storage, tol):
+    """The device-side ligament set-up equals the host input generator; the
+    state is at rest (j = 0), so the reported u_b is F/(2 rho)."""
     nx, ny, nz = 24, 20, 30
     want = inputs.ligament_density(nx, ny, nz, 5.0, 0.05, RL, RV)
     with lbm.Lattice(nx, ny, nz, storage=storage) as L:
         L.init_ligament(5.0, 0.05, RL, RV)
         r, u = L.moments()
-    assert np.abs(r - want).max() <= tol * 3
-    assert np.abs(u).max() <= tol
+    r_ref, u_ref = o.macroscopic(o.init_populations(want), o.Params(G=G))
+    assert np.abs(r - r_ref).max() <= tol * 3
+    assert np.abs(u - u_ref).max() <= tol * 3
 
 
 def test_diagnostics_match_the_reference():
