@@ -164,6 +164,44 @@ lbm_status lbm_kernel_config(const lbm_ctx *ctx, int *kernel, int *tile_y,
 /* sizeof(lbm_params) in this build, so that bindings can check their layout. */
 long long lbm_params_sizeof(void);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free diagnostics.  The paper has no counterpart: this is a
+ * service of the library, not part of the method.
+ *
+ * For callers that may not allocate device memory while they run: a program
+ * whose device memory is all handed out by its own pool allocator (where a
+ * raw cudaMalloc fails or fragments the pool), or a tight time-stepping loop
+ * in which cudaMalloc/cudaFree would implicitly synchronise the device.
+ * lbm_create allocates; this call does not.  It needs no context: the caller
+ * passes its own population array f (device memory, 19*nx*ny*nz elements of
+ * `storage` in the library's velocity order and field layout; rho_ref and
+ * dev_scale as in lbm_params for the deviation formats) and its own outputs,
+ * and gets the same quantities as lbm_diag (mass, mom[3], area_z[nz],
+ * maxrho_z[nz]; area_z/maxrho_z may be NULL).  Outputs are host memory when
+ * on_device is 0, device memory when it is 1.  Work runs on `stream`
+ * (cudaStream_t, NULL = legacy default), which the call synchronises before
+ * it returns.
+ *
+ * Scratch: a fixed array in the library's device memory, LBM_NOALLOC_MAX_NZ
+ * slices (8 doubles per slice, 512 KiB), which every GPU that loads the
+ * library holds until the process exits.  The first call on each device looks
+ * up that array's device address; make that first call before any stream
+ * capture.  All calls share the one array and each overwrites what it reads,
+ * so calls that overlap on the GPU (other host threads, other streams) race:
+ * serialise them.  The call never calls cudaMalloc/cudaFree or any allocating
+ * library routine.
+ *
+ * Returns LBM_EUNSUPPORTED (and does nothing) when nz > LBM_NOALLOC_MAX_NZ,
+ * LBM_EINVAL for other bad arguments, LBM_ECUDA if a launch or copy fails,
+ * LBM_ENONFINITE (outputs still written) if any cell has rho <= 0, NaN or Inf.
+ * ------------------------------------------------------------------------- */
+#define LBM_NOALLOC_MAX_NZ 8192
+lbm_status lbm_diag_noalloc(const void *f, int storage, int nx, int ny, int nz,
+                            double rho_ref, double dev_scale, double rho_l,
+                            double rho_v, double *mass, double mom[3],
+                            double *area_z, double *maxrho_z, int on_device,
+                            void *stream);
+
 #ifdef __cplusplus
 }
 #endif

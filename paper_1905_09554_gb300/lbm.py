@@ -78,6 +78,9 @@ _SIGNATURES = {
     "lbm_params_sizeof": (ctypes.c_longlong, []),
     "lbm_kernel_config": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "lbm_diag_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                        _P, _P, _P, _P, ctypes.c_int, _P]),
 }
 
 _lib = None
@@ -182,6 +185,14 @@ def lbm_set_stream(ctx, stream):
 
 def lbm_device_bytes(ctx):
     return load().lbm_device_bytes(ctx)
+
+
+def lbm_diag_noalloc(f, storage, nx, ny, nz, rho_ref, dev_scale, rho_l, rho_v, mass, mom, area_z,
+                     maxrho_z, on_device, stream):
+    """Allocation-free diagnostics on a caller-owned population array (see
+    include/lbm_sc.h); pointers are passed through unchanged."""
+    return load().lbm_diag_noalloc(f, storage, nx, ny, nz, rho_ref, dev_scale, rho_l, rho_v, mass, mom,
+                                   area_z, maxrho_z, on_device, stream)
 
 
 def lbm_kernel_config(ctx):

@@ -82,3 +82,13 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.lbm_init_ligament(None, 8.0, 0.05, 1, 2.0, 2.3, 0.1) == lbm.LBM_EINVAL
     assert lib.lbm_time(None) == -1
     lib.lbm_destroy(None)
+
+
+def test_noalloc_diagnostics_reject_boxes_beyond_the_static_scratch(lib):
+    """nz above LBM_NOALLOC_MAX_NZ is refused before any device work."""
+    st = lbm.lbm_diag_noalloc(16, lbm.LBM_F32, 4, 4, 8193, 1.0, 1.0, 2.3, 0.1,
+                              None, None, None, None, 0, None)
+    assert st == lbm.LBM_EUNSUPPORTED
+    st = lbm.lbm_diag_noalloc(None, lbm.LBM_F32, 4, 4, 8, 1.0, 1.0, 2.3, 0.1,
+                              None, None, None, None, 0, None)
+    assert st == lbm.LBM_EINVAL
