@@ -38,6 +38,7 @@ sys.path.insert(0, ROOT)
 METRIC = "D3Q19 SC-LBM MLUPS & % HBM peak; FP32/FP16 & batched vs FP64 at stated error"
 BYTES_PER_POP = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 FALLBACK_HBM_GBS = 6800.0
+KERNEL_NAMES = {1: "sc_step_kernel", 2: "sc_step_async_kernel", 3: "sc_step_pipe_kernel"}
 
 
 def parse_args():
@@ -287,7 +288,7 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None,
                 "peak_source": f"{src} HBM copy bandwidth",
-                "kernel": "sc_step_kernel", "algorithmic_bytes_per_cell": bpc,
+                "kernel": KERNEL_NAMES.get(L_info["kernel"], "sc_step_kernel"), "algorithmic_bytes_per_cell": bpc,
                 "kernel_ms": kernel_ms}
     traffic = load_traffic(args, ncell)
     if traffic is not None:
