@@ -19,6 +19,7 @@
 
 #include "../../include/lbm_sc.h"
 #include "codec.cuh"
+#include "diag_cell.cuh"
 #include "lattice.cuh"
 
 using namespace lbm;
@@ -51,15 +52,8 @@ slice_diag_noalloc_kernel(double* __restrict__ scratch, const typename Codec::S*
     double m = 0, jx = 0, jy = 0, jz = 0, area = 0, mx = 0, bad = 0;
     const double inv = 1.0 / (rho_l - rho_v);
     for (long long i = threadIdx.x; i < plane; i += kThreads) {
-        double r = 0, ax = 0, ay = 0, az = 0;
-        static_for<0, Q>([&](auto qc) {
-            constexpr int q = decltype(qc)::value;
-            const double fq = decode_rt<Codec>(fz + q * n + i, float(wq(q)), dev);
-            r += fq;
-            ax += cx(q) * fq;
-            ay += cy(q) * fq;
-            az += cz(q) * fq;
-        });
+        double r, ax, ay, az;
+        diag_cell<Codec>(fz + i, n, dev, r, ax, ay, az);
         m += r;
         jx += ax;
         jy += ay;

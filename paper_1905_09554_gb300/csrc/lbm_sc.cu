@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -12,8 +13,9 @@
 
 #include "../../include/lbm_sc.h"
 #include "codec.cuh"
+#include "diag_cell.cuh"
 #include "lattice.cuh"
-#include "step_kernel.cuh"
+#include "step_args.h"
 
 using namespace lbm;
 
@@ -35,8 +37,9 @@ struct lbm_ctx {
     long long own_bytes = 0;
     StepArgs args{};
     int zchunk = 0, tile_y = 8;
-    int kernel = 1;                   // 1 register-staged, 2 cp.async persistent
-    int grid = 0;                     // persistent grid size (kernel 2)
+    int kernel = 1;                   // 1 register-staged, 2 cp.async, 3 pipelined
+    int grid = 0;                     // persistent grid size (kernels 2, 3)
+    bool idx32 = false;               // 19 * cells fits 32-bit element offsets
     char err[512] = {0};
 
     lbm_status fail(lbm_status s, const char* fmt, ...) {
@@ -193,15 +196,8 @@ diag_kernel(double* __restrict__ out, const typename Codec::S* __restrict__ f, i
     double m = 0, jx = 0, jy = 0, jz = 0, area = 0, mx = 0, bad = 0;
     const double inv = 1.0 / (rho_l - rho_v);
     for (long long i = threadIdx.x; i < plane; i += DIAG_THREADS) {
-        double r = 0, ax = 0, ay = 0, az = 0;
-        static_for<0, Q>([&](auto qc) {
-            constexpr int q = decltype(qc)::value;
-            const double fq = decode_rt<Codec>(fz + q * n + i, float(wq(q)), dev);
-            r += fq;
-            ax += cx(q) * fq;
-            ay += cy(q) * fq;
-            az += cz(q) * fq;
-        });
+        double r, ax, ay, az;
+        diag_cell<Codec>(fz + i, n, dev, r, ax, ay, az);
         m += r;
         jx += ax;
         jy += ay;
@@ -240,102 +236,34 @@ int grid_for(long long work, int threads, int num_sms) {
 // ----------------------------------------------------------------------------
 // Typed dispatch
 // ----------------------------------------------------------------------------
-template <class Codec, int COLL, int TY>
-cudaError_t launch_step_t(const lbm_ctx* c, const void* src, void* dst) {
-    constexpr int TX = 32;
-    const StepArgs& a = c->args;
-    if constexpr (sizeof(typename Codec::S) >= 4) {
-        if (c->kernel == 3) {
-            sc_step_pipe_kernel<Codec, COLL, TX, TY><<<c->grid, TX * TY, PipeLayout<Codec, TX, TY>::bytes, c->stream>>>(
-                static_cast<const typename Codec::S*>(src), static_cast<typename Codec::S*>(dst), a);
-            return cudaGetLastError();
-        }
-    }
-    if constexpr (sizeof(typename Codec::S) >= 4 && (TY <= 8 || sizeof(typename Codec::S) == 4)) {
-        if (c->kernel == 2) {
-            sc_step_async_kernel<Codec, COLL, TX, TY><<<c->grid, TX * TY, AsyncLayout<Codec, TX, TY>::bytes, c->stream>>>(
-                static_cast<const typename Codec::S*>(src), static_cast<typename Codec::S*>(dst), a);
-            return cudaGetLastError();
-        }
-    }
-    dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + a.zchunk - 1) / a.zchunk);
-    sc_step_kernel<Codec, COLL, TX, TY><<<grid, TX * TY, 0, c->stream>>>(
-        static_cast<const typename Codec::S*>(src), static_cast<typename Codec::S*>(dst), a);
-    return cudaGetLastError();
-}
-
-// Prepare the cp.async kernel: opt in to its shared memory and size the
-// persistent grid from the occupancy calculator.  Returns 0 if the variant
-// cannot run for this storage/tile.
-template <class Codec, int COLL, int TY>
-int prepare_async_t(lbm_ctx* c) {
-    constexpr int TX = 32;
-    if constexpr (sizeof(typename Codec::S) >= 4) {
-        if (c->kernel == 3) {
-            using Lay = PipeLayout<Codec, TX, TY>;
-            auto kern = sc_step_pipe_kernel<Codec, COLL, TX, TY>;
-            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes) !=
-                cudaSuccess)
-                return 0;
-            int per_sm = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, Lay::bytes) != cudaSuccess)
-                return 0;
-            return per_sm;
-        }
-    }
-    if constexpr (sizeof(typename Codec::S) >= 4 && (TY <= 8 || sizeof(typename Codec::S) == 4)) {
-        using Lay = AsyncLayout<Codec, TX, TY>;
-        auto kern = sc_step_async_kernel<Codec, COLL, TX, TY>;
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes) != cudaSuccess)
-            return 0;
-        int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, Lay::bytes) != cudaSuccess ||
-            per_sm < 1)
-            return 0;
-        return per_sm;
-    }
-    return 0;
-}
-
-template <class Codec, int COLL>
-int prepare_async_c(lbm_ctx* c) {
-    switch (c->tile_y) {
-        case 4: return prepare_async_t<Codec, COLL, 4>(c);
-        case 16: return prepare_async_t<Codec, COLL, 16>(c);
-        default: return prepare_async_t<Codec, COLL, 8>(c);
-    }
+StepLaunch step_launch(const lbm_ctx* c) {
+    StepLaunch l;
+    l.args = c->args;
+    l.kernel = c->kernel;
+    l.tile_y = c->tile_y;
+    l.grid = c->grid;
+    l.idx32 = c->idx32;
+    l.coll = c->p.collision == LBM_MRT_GUO ? COLL_MRT : COLL_SRT;
+    l.stream = c->stream;
+    return l;
 }
 
 int prepare_async(lbm_ctx* c) {
-    const bool mrt = c->p.collision == LBM_MRT_GUO;
+    const StepLaunch l = step_launch(c);
     switch (c->p.storage) {
-        case LBM_F64: return mrt ? prepare_async_c<CodecF64, COLL_MRT>(c) : prepare_async_c<CodecF64, COLL_SRT>(c);
-        case LBM_F32: return mrt ? prepare_async_c<CodecF32, COLL_MRT>(c) : prepare_async_c<CodecF32, COLL_SRT>(c);
+        case LBM_F64: return prepare_step_f64(l);
+        case LBM_F32: return prepare_step_f32(l);
         default: return 0;
     }
 }
 
-template <class Codec, int COLL>
-cudaError_t launch_step_c(const lbm_ctx* c, const void* src, void* dst) {
-    switch (c->tile_y) {
-        case 4: return launch_step_t<Codec, COLL, 4>(c, src, dst);
-        case 16: return launch_step_t<Codec, COLL, 16>(c, src, dst);
-        default: return launch_step_t<Codec, COLL, 8>(c, src, dst);
-    }
-}
-
-template <class Codec>
-cudaError_t launch_step_s(const lbm_ctx* c, const void* src, void* dst) {
-    return c->p.collision == LBM_MRT_GUO ? launch_step_c<Codec, COLL_MRT>(c, src, dst)
-                                         : launch_step_c<Codec, COLL_SRT>(c, src, dst);
-}
-
 cudaError_t launch_step(const lbm_ctx* c, const void* src, void* dst) {
+    const StepLaunch l = step_launch(c);
     switch (c->p.storage) {
-        case LBM_F64: return launch_step_s<CodecF64>(c, src, dst);
-        case LBM_F16_DEV: return launch_step_s<CodecF16Dev>(c, src, dst);
-        case LBM_BF16_DEV: return launch_step_s<CodecBF16Dev>(c, src, dst);
-        default: return launch_step_s<CodecF32>(c, src, dst);
+        case LBM_F64: return launch_step_f64(l, src, dst);
+        case LBM_F16_DEV: return launch_step_f16(l, src, dst);
+        case LBM_BF16_DEV: return launch_step_bf16(l, src, dst);
+        default: return launch_step_f32(l, src, dst);
     }
 }
 
@@ -455,6 +383,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     c->p = *p;
     c->stream = static_cast<cudaStream_t>(p->stream);
     c->n = n;
+    c->idx32 = (long long)Q * n < (1LL << 31);
     c->elem = p->storage == LBM_F64 ? 8 : (p->storage == LBM_F32 ? 4 : 2);
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -515,11 +444,13 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     a.dev.rho_ref = float(p->rho_ref);
     a.dev.scale = float(p->dev_scale);
     a.dev.inv_scale = float(1.0 / p->dev_scale);
-    // Auto launch shape (measured on GB300 at 256x256x575): FP32 SRT runs the
-    // pipelined kernel on 32x16 tiles; MRT and the other storage types run the
-    // register-staged kernel on 32x4 tiles.
-    const bool pipe_default = p->storage == LBM_F32 && p->collision == LBM_SRT_SHIFT;
-    c->tile_y = p->tile_y ? p->tile_y : ((p->kernel == 3 || (p->kernel == 0 && pipe_default)) ? 16 : 4);
+    // Auto launch shape (measured on GB300 at 256x256x575): FP32 runs the
+    // pipelined kernel, on 32x16 tiles for SRT and 32x4 tiles for MRT (whose
+    // collision needs more registers per cell); the other storage types run
+    // the register-staged kernel on 32x4 tiles.
+    const bool pipe_default = p->storage == LBM_F32;
+    const bool wide = p->collision == LBM_SRT_SHIFT && (p->kernel == 3 || (p->kernel == 0 && pipe_default));
+    c->tile_y = p->tile_y ? p->tile_y : (wide ? 16 : 4);
     if (p->kernel < 0 || p->kernel > 3) {
         snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel must be 0, 1, 2 or 3");
         lbm_destroy(c);

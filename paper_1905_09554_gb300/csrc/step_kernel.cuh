@@ -23,23 +23,9 @@
 
 #include "codec.cuh"
 #include "lattice.cuh"
+#include "step_args.h"
 
 namespace lbm {
-
-enum { COLL_SRT = 0, COLL_MRT = 1 };
-
-struct StepArgs {
-    int nx, ny, nz;
-    int zchunk;           // planes per block (work item) along z
-    int tiles_x, n_tiles; // xy tiles of the persistent kernel
-    int n_items;          // n_tiles * number of z chunks
-    long long n;          // cells = nx*ny*nz (population stride)
-    double G;             // interaction strength G0
-    double tau, omega;    // SRT relaxation time and 1/tau
-    double rho0, inv_rho0;
-    double s[Q];          // MRT rates, moment order
-    DevParams dev;
-};
 
 template <class R>
 __device__ __forceinline__ R psi_of(R rho, R rho0, R inv_rho0);
@@ -174,11 +160,11 @@ __device__ __forceinline__ typename Codec::R cell_density(const typename Codec::
 
 // Force from the psi ring (planes z-1, z, z+1 of the tile + ring), collision
 // of the cell's populations fc, and push to x + c_a in `dst`.
-template <class Codec, int COLL, int PX>
+template <class Codec, int COLL, int PX, class I = long long>
 __device__ __forceinline__ void update_cell(typename Codec::R (&fc)[Q], const typename Codec::R* pm,
                                             const typename Codec::R* p0, const typename Codec::R* pp,
-                                            int slot, typename Codec::S* __restrict__ dst, long long n,
-                                            const long long (&zoff)[3], const long long (&yoff)[3],
+                                            int slot, typename Codec::S* __restrict__ dst, I n,
+                                            const I (&zoff)[3], const I (&yoff)[3],
                                             const int (&xidx)[3], const StepArgs& a) {
     using R = typename Codec::R;
     const R* pl[3] = {pm, p0, pp};
@@ -200,8 +186,8 @@ __device__ __forceinline__ void update_cell(typename Codec::R (&fc)[Q], const ty
     // Eq. LBE streaming: f_a(x + c_a, t + 1) = f*_a(x, t).
     static_for<0, Q>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
-        const long long idx = zoff[cz(q) + 1] + yoff[cy(q) + 1] + xidx[cx(q) + 1];
-        Codec::template store<q>(dst + q * n + idx, fc[q], a.dev);
+        const I idx = zoff[cz(q) + 1] + yoff[cy(q) + 1] + xidx[cx(q) + 1];
+        Codec::template store<q>(dst + (I(q) * n + idx), fc[q], a.dev);
     });
 }
 
@@ -493,8 +479,10 @@ struct PipeLayout {
 };
 
 // Register budget: at most 65536 / (512 threads) = 128 registers per thread
-// so that 512 threads per SM stay resident.
-template <class Codec, int COLL, int TX, int TY>
+// so that 512 threads per SM stay resident.  I is the element-offset type:
+// int when 19 * cells fits in 31 bits (fewer registers and address
+// instructions), long long otherwise.
+template <class Codec, int COLL, int TX, int TY, class I>
 __global__ void __launch_bounds__(TX * TY, (TX * TY >= 512) ? 1 : 512 / (TX * TY))
 sc_step_pipe_kernel(const typename Codec::S* __restrict__ src, typename Codec::S* __restrict__ dst,
                     const StepArgs a) {
@@ -510,8 +498,8 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src, typename Codec::S
     const int tid = threadIdx.x;
     const int lx = tid % TX, ly = tid / TX;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const long long n = a.n;
-    const long long plane = (long long)nx * ny;
+    const I n = I(a.n);
+    const I plane = I(nx) * I(ny);
     const R rho0 = R(a.rho0), inv_rho0 = R(a.inv_rho0);
     const DevParams dev = a.dev;
     const int my_slot = (ly + 1) * PX + (lx + 1);
@@ -532,11 +520,11 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src, typename Codec::S
 
         const int gx = wrap_index(x0 + lx, nx), gy = wrap_index(y0 + ly, ny);
         const bool active = (x0 + lx < nx) && (y0 + ly < ny);
-        const long long my_xy = (long long)gy * nx + gx;
-        const long long h_xy = (h_slot >= 0) ? (long long)wrap_index(y0 + hy, ny) * nx + wrap_index(x0 + hx, nx) : 0;
+        const I my_xy = I(gy) * I(nx) + I(gx);
+        const I h_xy = (h_slot >= 0) ? I(wrap_index(y0 + hy, ny)) * I(nx) + I(wrap_index(x0 + hx, nx)) : I(0);
         const int xp = (gx + 1 == nx) ? 0 : gx + 1, xm = (gx == 0) ? nx - 1 : gx - 1;
         const int yp = (gy + 1 == ny) ? 0 : gy + 1, ym = (gy == 0) ? ny - 1 : gy - 1;
-        const long long yoff[3] = {(long long)ym * nx, (long long)gy * nx, (long long)yp * nx};
+        const I yoff[3] = {I(ym) * I(nx), I(gy) * I(nx), I(yp) * I(nx)};
         const int xidx[3] = {xm, gx, xp};
 
         auto wrapz = [&](int z) { return z < 0 ? z + nz : (z >= nz ? z - nz : z); };
@@ -544,11 +532,11 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src, typename Codec::S
         auto slot_of = [&](int z) { return (z - zs + 1) & (L::NSLOT - 1); };
         auto issue_halo = [&](int z) {
             if (h_slot >= 0) {
-                const S* base = src + (long long)wrapz(z) * plane + h_xy;
+                const S* base = src + (I(wrapz(z)) * plane + h_xy);
                 S* st = hstage + stage_of(z) * (Q * NH);
                 static_for<0, Q>([&](auto qc) {
                     constexpr int q = decltype(qc)::value;
-                    async_copy::copy<sizeof(S)>(st + q * NH + tid, base + q * n);
+                    async_copy::copy<sizeof(S)>(st + q * NH + tid, base + I(q) * n);
                 });
             }
             async_copy::commit();
@@ -565,10 +553,10 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src, typename Codec::S
             }
         };
         auto load_plane = [&](R (&f)[Q], int z) {
-            const S* base = src + (long long)wrapz(z) * plane + my_xy;
+            const S* base = src + (I(wrapz(z)) * plane + my_xy);
             static_for<0, Q>([&](auto qc) {
                 constexpr int q = decltype(qc)::value;
-                f[q] = Codec::template load<q>(base + q * n, dev);
+                f[q] = Codec::template load<q>(base + I(q) * n, dev);
             });
         };
         auto own_psi = [&](const R (&f)[Q], int z) {
@@ -579,26 +567,11 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src, typename Codec::S
             });
             ring[slot_of(z) * PLANE + my_slot] = psi_of<R>(r, rho0, inv_rho0);
         };
-
-        __syncthreads();  // the previous item's readers of the psi ring are done
-        issue_halo(zs - 1);
-        issue_halo(zs);
-        issue_halo(zs + 1);
-        R fc[Q], fn[Q];
-        load_plane(fc, zs - 1);
-        own_psi(fc, zs - 1);
-        load_plane(fc, zs);
-        load_plane(fn, zs + 1);
-        async_copy::wait<2>();
-        halo_psi(zs - 1);
-        async_copy::wait<1>();
-        halo_psi(zs);
-        own_psi(fc, zs);
-        own_psi(fn, zs + 1);
-
-        for (int z = zs; z < ze; ++z) {
+        // One plane: loads of z+2 go out before the collision of z and are
+        // consumed after it.  fc holds plane z, fn plane z+1, fl receives z+2;
+        // the caller rotates the three arrays instead of copying them.
+        auto body = [&](R (&fc)[Q], R (&fn)[Q], R (&fl)[Q], int z) {
             const bool more = z + 2 <= ze;
-            R fl[Q];
             if (more) load_plane(fl, z + 2);
             if (more) issue_halo(z + 2);
             else async_copy::commit();
@@ -608,16 +581,35 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src, typename Codec::S
             if (active) {
                 const int zm = (z == 0) ? nz - 1 : z - 1;
                 const int zn = (z + 1 == nz) ? 0 : z + 1;
-                const long long zoff[3] = {(long long)zm * plane, (long long)z * plane, (long long)zn * plane};
-                update_cell<Codec, COLL, PX>(fc, ring + slot_of(z - 1) * PLANE, ring + slot_of(z) * PLANE,
-                                             ring + slot_of(z + 1) * PLANE, my_slot, dst, n, zoff, yoff, xidx, a);
+                const I zoff[3] = {I(zm) * plane, I(z) * plane, I(zn) * plane};
+                update_cell<Codec, COLL, PX, I>(fc, ring + slot_of(z - 1) * PLANE, ring + slot_of(z) * PLANE,
+                                                ring + slot_of(z + 1) * PLANE, my_slot, dst, n, zoff, yoff, xidx,
+                                                a);
             }
             if (more) own_psi(fl, z + 2);
-            static_for<0, Q>([&](auto qc) {
-                constexpr int q = decltype(qc)::value;
-                fc[q] = fn[q];
-                if (more) fn[q] = fl[q];
-            });
+            (void)fn;
+        };
+
+        __syncthreads();  // the previous item's readers of the psi ring are done
+        issue_halo(zs - 1);
+        issue_halo(zs);
+        issue_halo(zs + 1);
+        R fa[Q], fb[Q], fcc[Q];
+        load_plane(fa, zs - 1);
+        own_psi(fa, zs - 1);
+        load_plane(fa, zs);
+        load_plane(fb, zs + 1);
+        async_copy::wait<2>();
+        halo_psi(zs - 1);
+        async_copy::wait<1>();
+        halo_psi(zs);
+        own_psi(fa, zs);
+        own_psi(fb, zs + 1);
+
+        for (int z = zs; z < ze; z += 3) {
+            body(fa, fb, fcc, z);
+            if (z + 1 < ze) body(fb, fcc, fa, z + 1);
+            if (z + 2 < ze) body(fcc, fa, fb, z + 2);
         }
     }
     async_copy::wait<0>();
