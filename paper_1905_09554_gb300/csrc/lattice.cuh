@@ -78,6 +78,18 @@ __host__ __device__ constexpr int mrt_norm(int k) {
     return s;
 }
 
+// True when moment k is odd in c: opposite velocities (q, q+1) carry opposite
+// coefficients (momentum, heat flux and the third-order m moments).
+__host__ __device__ constexpr bool mrt_moment_is_odd(int k) {
+    bool odd = true;
+    for (int q = 1; q < Q; q += 2) odd = odd && (mrt_coef(k, q + 1) == -mrt_coef(k, q));
+    return odd && mrt_coef(k, 0) == 0;
+}
+
+static_assert(mrt_moment_is_odd(3) && mrt_moment_is_odd(8) && mrt_moment_is_odd(16) && mrt_moment_is_odd(18),
+              "odd moments");
+static_assert(!mrt_moment_is_odd(0) && !mrt_moment_is_odd(11) && !mrt_moment_is_odd(12) && !mrt_moment_is_odd(15),
+              "even moments");
 static_assert(mrt_norm(0) == 19 && mrt_norm(1) == 2394 && mrt_norm(2) == 252, "basis");
 static_assert(mrt_norm(4) == 40 && mrt_norm(10) == 72 && mrt_norm(16) == 8, "basis");
 

@@ -44,30 +44,38 @@ __device__ __forceinline__ int wrap_index(int i, int n) {
 }
 
 // SRT with shifted equilibrium (Eq. vel_shift): u' = (j + tau F)/rho,
-// f* = f + (f_eq(rho, u') - f)/tau.
+// f* = f + (f_eq(rho, u') - f)/tau.  Velocities come in +/- pairs (q, q+1),
+// whose equilibria share the even part A and differ by the sign of the odd
+// part B: f_eq = A +/- B.
 template <class R>
 __device__ __forceinline__ void collide_srt(R (&f)[Q], R Fx, R Fy, R Fz, R tau, R omega) {
-    R rho = R(0), jx = R(0), jy = R(0), jz = R(0);
-    static_for<0, Q>([&](auto qc) {
-        constexpr int q = decltype(qc)::value;
-        rho += f[q];
-        if constexpr (cx(q) != 0) jx += R(cx(q)) * f[q];
-        if constexpr (cy(q) != 0) jy += R(cy(q)) * f[q];
-        if constexpr (cz(q) != 0) jz += R(cz(q)) * f[q];
+    R rho = f[0], jx = R(0), jy = R(0), jz = R(0);
+    static_for<0, 9>([&](auto pc) {
+        constexpr int q = 2 * decltype(pc)::value + 1;
+        const R sum = f[q] + f[q + 1], dif = f[q] - f[q + 1];
+        rho += sum;
+        if constexpr (cx(q) != 0) jx += R(cx(q)) * dif;
+        if constexpr (cy(q) != 0) jy += R(cy(q)) * dif;
+        if constexpr (cz(q) != 0) jz += R(cz(q)) * dif;
     });
     const R inv_rho = R(1) / rho;
     const R ux = (jx + tau * Fx) * inv_rho;
     const R uy = (jy + tau * Fy) * inv_rho;
     const R uz = (jz + tau * Fz) * inv_rho;
     const R usq = R(1.5) * (ux * ux + uy * uy + uz * uz);
-    static_for<0, Q>([&](auto qc) {
-        constexpr int q = decltype(qc)::value;
+    const R base = R(1) - usq;
+    f[0] += omega * (R(wq(0)) * rho * base - f[0]);
+    static_for<0, 9>([&](auto pc) {
+        constexpr int q = 2 * decltype(pc)::value + 1;
         R cu = R(0);
         if constexpr (cx(q) != 0) cu += R(cx(q)) * ux;
         if constexpr (cy(q) != 0) cu += R(cy(q)) * uy;
         if constexpr (cz(q) != 0) cu += R(cz(q)) * uz;
-        const R feq = R(wq(q)) * rho * (R(1) + R(3) * cu + R(4.5) * cu * cu - usq);
-        f[q] += omega * (feq - f[q]);
+        const R wr = R(wq(q)) * rho;
+        const R A = wr * (base + R(4.5) * cu * cu);
+        const R B = wr * (R(3) * cu);
+        f[q] += omega * ((A + B) - f[q]);
+        f[q + 1] += omega * ((A - B) - f[q + 1]);
     });
 }
 
@@ -78,16 +86,30 @@ __device__ __forceinline__ void collide_srt(R (&f)[Q], R Fx, R Fy, R Fz, R tau, 
 // Conserved moments: the rho row vanishes and the j rows reduce to -F.
 template <class R>
 __device__ __forceinline__ void collide_mrt(R (&f)[Q], R Fx, R Fy, R Fz, const double (&s)[Q]) {
+    // Pair sums feed the moments that are even in c, pair differences the
+    // odd ones (M[k][q+1] = +/- M[k][q] for the opposite velocity q+1).
+    R ps[9], pd[9];
+    static_for<0, 9>([&](auto pc) {
+        constexpr int p = decltype(pc)::value, q = 2 * p + 1;
+        ps[p] = f[q] + f[q + 1];
+        pd[p] = f[q] - f[q + 1];
+    });
     R m[Q];
     static_for<0, Q>([&](auto kc) {
         constexpr int k = decltype(kc)::value;
+        constexpr bool odd = mrt_moment_is_odd(k);
         R acc = R(0);
-        static_for<0, Q>([&](auto qc) {
-            constexpr int q = decltype(qc)::value;
+        if constexpr (!odd) {
+            constexpr int c0 = mrt_coef(k, 0);
+            if constexpr (c0 != 0) acc = R(c0) * f[0];
+        }
+        static_for<0, 9>([&](auto pc) {
+            constexpr int p = decltype(pc)::value, q = 2 * p + 1;
             constexpr int c = mrt_coef(k, q);
-            if constexpr (c == 1) acc += f[q];
-            else if constexpr (c == -1) acc -= f[q];
-            else if constexpr (c != 0) acc += R(c) * f[q];
+            const R v = odd ? pd[p] : ps[p];
+            if constexpr (c == 1) acc += v;
+            else if constexpr (c == -1) acc -= v;
+            else if constexpr (c != 0) acc += R(c) * v;
         });
         m[k] = acc;
     });
@@ -132,17 +154,39 @@ __device__ __forceinline__ void collide_mrt(R (&f)[Q], R Fx, R Fy, R Fz, const d
             d[k] = (sk * (m[k] - meq[k]) - (R(1) - R(0.5) * sk) * sg[k]) * R(1.0 / mrt_norm(k));
         }
     });
-    static_for<0, Q>([&](auto qc) {
-        constexpr int q = decltype(qc)::value;
-        R acc = R(0);
+    // f* = f - M^T d: the even moments give the common part E of a velocity
+    // pair, the odd ones the antisymmetric part O (f*_q = f_q - E - O,
+    // f*_{q+1} = f_{q+1} - E + O).
+    {
+        R e0 = R(0);
+        static_for<1, Q>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            constexpr int c = mrt_coef(k, 0);
+            if constexpr (c != 0) e0 += R(c) * d[k];
+        });
+        f[0] -= e0;
+    }
+    static_for<0, 9>([&](auto pc) {
+        constexpr int q = 2 * decltype(pc)::value + 1;
+        R E = R(0), O = R(0);
         static_for<1, Q>([&](auto kc) {
             constexpr int k = decltype(kc)::value;
             constexpr int c = mrt_coef(k, q);
-            if constexpr (c == 1) acc += d[k];
-            else if constexpr (c == -1) acc -= d[k];
-            else if constexpr (c != 0) acc += R(c) * d[k];
+            constexpr bool odd = mrt_coef(k, q + 1) == -c && c != 0;
+            if constexpr (c != 0) {
+                if constexpr (odd) {
+                    if constexpr (c == 1) O += d[k];
+                    else if constexpr (c == -1) O -= d[k];
+                    else O += R(c) * d[k];
+                } else {
+                    if constexpr (c == 1) E += d[k];
+                    else if constexpr (c == -1) E -= d[k];
+                    else E += R(c) * d[k];
+                }
+            }
         });
-        f[q] -= acc;
+        f[q] -= E + O;
+        f[q + 1] -= E - O;
     });
 }
 
