@@ -165,6 +165,46 @@ lbm_status lbm_kernel_config(const lbm_ctx *ctx, int *kernel, int *tile_y,
 long long lbm_params_sizeof(void);
 
 /* ---------------------------------------------------------------------------
+ * Batches: many independent periodic boxes (uneven sizes) advanced together.
+ * The method is the paper's step (Sec. 2) applied to each box; batching is a
+ * GPU execution form, not in the paper.
+ * ------------------------------------------------------------------------- */
+typedef struct lbm_batch lbm_batch;
+
+/* Create `count` boxes sharing the physics of *p (G, collision, tau, rates,
+ * psi, storage: FP32 or FP64; p->nx/ny/nz are ignored; p->tile_y / zchunk
+ * choose the initial launch shape, 0 = default).  dims[3*i + 0..2] are box
+ * i's nx, ny, nz (each box needs 19 * cells < 2^31).  One allocation per
+ * population copy holds every box (256-byte aligned per box).  If p->stream
+ * is NULL the batch creates its own stream (needed to capture the step graph).
+ * On failure *out is NULL and lbm_batch_last_error(NULL) has the message. */
+lbm_status lbm_batch_create(const lbm_params *p, int count, const int *dims,
+                            lbm_batch **out);
+void lbm_batch_destroy(lbm_batch *b);                  /* NULL-safe */
+const char *lbm_batch_last_error(const lbm_batch *b);
+
+/* Context view of box i, owned by the batch: use it with lbm_init_ligament,
+ * lbm_set_density, lbm_set/get_populations, lbm_moments, lbm_diag.  Stepping
+ * it alone (lbm_step) returns LBM_EINVAL; lbm_destroy ignores it. */
+lbm_status lbm_batch_box(lbm_batch *b, int i, lbm_ctx **view);
+
+/* Advance every box n >= 0 steps with one kernel launch per step over the
+ * work items (xy tile, z chunk) of all boxes; pairs of steps are replayed
+ * from a captured CUDA graph. */
+lbm_status lbm_batch_step(lbm_batch *b, long n);
+
+/* Autotune the launch shape: times trial_steps steps for each tile height in
+ * {4, 8, 16} and z chunk in {8, 16, 32, 64}, keeps the fastest and reports it
+ * (any pointer may be NULL).  The trial steps overwrite the populations:
+ * tune first, then initialise the boxes. */
+lbm_status lbm_batch_tune(lbm_batch *b, int trial_steps, int *tile_y,
+                          int *zchunk, double *ms_per_step);
+
+/* Current launch shape, grid size and total cells. */
+lbm_status lbm_batch_config(const lbm_batch *b, int *tile_y, int *zchunk,
+                            int *grid, long long *cells);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free diagnostics.  The paper has no counterpart: this is a
  * service of the library, not part of the method.
  *

@@ -19,6 +19,8 @@
 
 using namespace lbm;
 
+struct lbm_batch;
+
 struct lbm_ctx {
     lbm_params p;
     cudaStream_t stream = nullptr;
@@ -41,6 +43,7 @@ struct lbm_ctx {
     int grid = 0;                     // persistent grid size (kernels 2, 3)
     bool idx32 = false;               // 19 * cells fits 32-bit element offsets
     char err[512] = {0};
+    lbm_batch* batch = nullptr;       // set when the context is a view of a batch box
 
     lbm_status fail(lbm_status s, const char* fmt, ...) {
         va_list ap;
@@ -501,7 +504,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
 }
 
 void lbm_destroy(lbm_ctx* c) {
-    if (!c) return;
+    if (!c || c->batch) return;  // batch boxes are destroyed with their batch
     cudaStreamSynchronize(c->stream);
     if (c->own_f) {
         cudaFree(c->f[0]);
@@ -650,6 +653,7 @@ lbm_status lbm_get_populations(lbm_ctx* c, double* f, int on_device) {
 lbm_status lbm_step(lbm_ctx* c, long nsteps) {
     if (!c) return LBM_EINVAL;
     if (nsteps < 0) return c->fail(LBM_EINVAL, "lbm_step: n must be >= 0");
+    if (c->batch) return c->fail(LBM_EINVAL, "lbm_step: this context is a box of a batch; use lbm_batch_step");
     for (long k = 0; k < nsteps; ++k) {
         cudaError_t e = launch_step(c, c->f[c->cur], c->f[c->cur ^ 1]);
         if (e != cudaSuccess) return c->fail(LBM_ECUDA, "step kernel launch failed: %s", cudaGetErrorString(e));
@@ -734,6 +738,318 @@ lbm_status lbm_diag(lbm_ctx* c, double rho_l, double rho_v, double* mass, double
     }
     if (bad > 0 || !std::isfinite(m))
         return c->fail(LBM_ENONFINITE, "lbm_diag: %.0f cells with rho <= 0 or non-finite at step %ld", bad, c->t);
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------------------
+// Batches of independent boxes
+// ----------------------------------------------------------------------------
+struct lbm_batch {
+    lbm_params p;                     // shared parameters (box sizes per box)
+    int count = 0;
+    std::vector<lbm_ctx*> box;        // per-box views over the shared copies
+    std::vector<long long> base;      // element offset of each box
+    void* f[2] = {nullptr, nullptr};
+    size_t bytes = 0;                 // per copy
+    int cur = 0;
+    long t = 0;
+    long long cells = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    int tile_y = 8, zchunk = 32, grid = 0;
+    BatchArgs bargs{};
+    BatchBox* boxes_dev = nullptr;
+    StepArgs phys{};
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // two-step cycle starting from copy 0 / 1
+    char err[512] = {0};
+
+    lbm_status fail(lbm_status s, const char* fmt, ...) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(err, sizeof(err), fmt, ap);
+        va_end(ap);
+        return s;
+    }
+};
+
+namespace {
+
+StepLaunch batch_launch(const lbm_batch* b) {
+    StepLaunch l;
+    l.args = b->phys;
+    l.kernel = 3;
+    l.tile_y = b->tile_y;
+    l.grid = b->grid;
+    l.idx32 = true;
+    l.coll = b->p.collision == LBM_MRT_GUO ? COLL_MRT : COLL_SRT;
+    l.stream = b->stream;
+    return l;
+}
+
+cudaError_t batch_launch_step(const lbm_batch* b, int from) {
+    const StepLaunch l = batch_launch(b);
+    if (b->p.storage == LBM_F64) return launch_batch_step_f64(l, b->bargs, b->f[from], b->f[from ^ 1]);
+    return launch_batch_step_f32(l, b->bargs, b->f[from], b->f[from ^ 1]);
+}
+
+void batch_drop_graphs(lbm_batch* b) {
+    for (auto& g : b->graph) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+}
+
+// (Re)build the work-item table for tile height ty and chunk zc, upload it and
+// size the persistent grid.
+lbm_status batch_configure(lbm_batch* b, int ty, int zc) {
+    const StepLaunch probe = [&] {
+        StepLaunch l = batch_launch(b);
+        l.tile_y = ty;
+        return l;
+    }();
+    const int per_sm = b->p.storage == LBM_F64 ? prepare_batch_step_f64(probe) : prepare_batch_step_f32(probe);
+    if (per_sm < 1) return b->fail(LBM_ECUDA, "batch kernel cannot be resident (tile_y %d)", ty);
+    std::vector<BatchBox> boxes(b->count);
+    int items = 0;
+    for (int i = 0; i < b->count; ++i) {
+        const lbm_params& q = b->box[i]->p;
+        BatchBox& bx = boxes[i];
+        bx.nx = q.nx;
+        bx.ny = q.ny;
+        bx.nz = q.nz;
+        bx.tiles_x = (q.nx + 31) / 32;
+        bx.n_tiles = bx.tiles_x * ((q.ny + ty - 1) / ty);
+        bx.zchunk = zc < q.nz ? zc : q.nz;
+        bx.item_begin = items;
+        bx.base = b->base[i];
+        bx.n = (long long)q.nx * q.ny * q.nz;
+        items += bx.n_tiles * ((q.nz + bx.zchunk - 1) / bx.zchunk);
+    }
+    LBM_CUDA(b, cudaMemcpyAsync(b->boxes_dev, boxes.data(), sizeof(BatchBox) * b->count, cudaMemcpyHostToDevice,
+                                b->stream));
+    LBM_CUDA(b, cudaStreamSynchronize(b->stream));
+    b->tile_y = ty;
+    b->zchunk = zc;
+    b->bargs.nbox = b->count;
+    b->bargs.n_items = items;
+    b->bargs.boxes = b->boxes_dev;
+    b->grid = per_sm * b->num_sms < items ? per_sm * b->num_sms : items;
+    batch_drop_graphs(b);
+    return LBM_OK;
+}
+
+lbm_status batch_build_graph(lbm_batch* b, int from) {
+    cudaGraph_t g = nullptr;
+    LBM_CUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e1 = batch_launch_step(b, from);
+    cudaError_t e2 = batch_launch_step(b, from ^ 1);
+    cudaError_t e3 = cudaStreamEndCapture(b->stream, &g);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return b->fail(LBM_ECUDA, "capturing the batch step graph failed: %s",
+                       cudaGetErrorString(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3)));
+    }
+    cudaError_t e = cudaGraphInstantiate(&b->graph[from], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return b->fail(LBM_ECUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_create(const lbm_params* p, int count, const int* dims, lbm_batch** out) {
+    g_create_err[0] = 0;
+    if (!out) return create_fail(LBM_EINVAL, "lbm_batch_create: out is NULL");
+    *out = nullptr;
+    if (!p || !dims || count < 1) return create_fail(LBM_EINVAL, "lbm_batch_create: need params, dims and count >= 1");
+    if (p->storage != LBM_F32 && p->storage != LBM_F64)
+        return create_fail(LBM_EINVAL, "lbm_batch_create: batches support FP32 and FP64 storage");
+    if (p->f_a || p->f_b) return create_fail(LBM_EINVAL, "lbm_batch_create: the batch allocates its own copies");
+    lbm_batch* b = new (std::nothrow) lbm_batch();
+    if (!b) return create_fail(LBM_ENOMEM, "lbm_batch_create: host allocation failed");
+    b->p = *p;
+    b->count = count;
+    const size_t elem = p->storage == LBM_F64 ? 8 : 4;
+    b->base.resize(count);
+    long long off = 0;
+    for (int i = 0; i < count; ++i) {
+        const int nx = dims[3 * i], ny = dims[3 * i + 1], nz = dims[3 * i + 2];
+        if (nx < 1 || ny < 1 || nz < 1) {
+            delete b;
+            return create_fail(LBM_EINVAL, "lbm_batch_create: box sizes must be >= 1");
+        }
+        const long long n = (long long)nx * ny * nz;
+        if ((long long)Q * n >= (1LL << 31)) {
+            delete b;
+            return create_fail(LBM_EINVAL, "lbm_batch_create: a box needs 19 * cells < 2^31");
+        }
+        b->base[i] = off;
+        b->cells += n;
+        // keep every box's copy 256-byte aligned
+        const long long per = (long long)Q * n;
+        const long long align = 256 / (long long)elem;
+        off += (per + align - 1) / align * align;
+    }
+    b->bytes = (size_t)off * elem;
+    cudaError_t e = cudaSuccess;
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) {
+        if (p->stream) {
+            b->stream = static_cast<cudaStream_t>(p->stream);
+        } else {  // graph capture needs a stream other than the legacy default
+            e = cudaStreamCreate(&b->stream);
+            b->own_stream = (e == cudaSuccess);
+        }
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->f[0], b->bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&b->f[1], b->bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&b->boxes_dev, sizeof(BatchBox) * count);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->f[0], 0, b->bytes, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->f[1], 0, b->bytes, b->stream);
+    if (e != cudaSuccess) {
+        snprintf(g_create_err, sizeof(g_create_err), "lbm_batch_create: %s", cudaGetErrorString(e));
+        lbm_batch_destroy(b);
+        return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+    }
+    b->box.assign(count, nullptr);
+    for (int i = 0; i < count; ++i) {
+        lbm_params q = *p;
+        q.nx = dims[3 * i];
+        q.ny = dims[3 * i + 1];
+        q.nz = dims[3 * i + 2];
+        q.stream = b->stream;
+        q.f_a = static_cast<char*>(b->f[0]) + (size_t)b->base[i] * elem;
+        q.f_b = static_cast<char*>(b->f[1]) + (size_t)b->base[i] * elem;
+        q.kernel = 1;
+        q.zchunk = 0;
+        q.tile_y = 0;
+        lbm_ctx* c = nullptr;
+        lbm_status st = lbm_create(&q, &c);
+        if (st != LBM_OK) {
+            lbm_batch_destroy(b);
+            return st;  // g_create_err holds the box's message
+        }
+        c->batch = b;
+        b->box[i] = c;
+    }
+    b->phys = b->box[0]->args;
+    const int ty = p->tile_y ? p->tile_y : (p->collision == LBM_MRT_GUO ? 4 : 8);
+    const int zc = p->zchunk ? p->zchunk : 32;
+    lbm_status st = batch_configure(b, ty, zc);
+    if (st != LBM_OK) {
+        snprintf(g_create_err, sizeof(g_create_err), "%s", b->err);
+        lbm_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_drop_graphs(b);
+    for (lbm_ctx* c : b->box) {
+        if (c) {
+            c->batch = nullptr;
+            lbm_destroy(c);
+        }
+    }
+    cudaFree(b->f[0]);
+    cudaFree(b->f[1]);
+    cudaFree(b->boxes_dev);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err : g_create_err; }
+
+lbm_status lbm_batch_box(lbm_batch* b, int i, lbm_ctx** view) {
+    if (!b || !view) return LBM_EINVAL;
+    if (i < 0 || i >= b->count) return b->fail(LBM_EINVAL, "lbm_batch_box: index %d out of range", i);
+    *view = b->box[i];
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, long n) {
+    if (!b) return LBM_EINVAL;
+    if (n < 0) return b->fail(LBM_EINVAL, "lbm_batch_step: n must be >= 0");
+    while (n >= 2) {
+        if (!b->graph[b->cur]) {
+            lbm_status st = batch_build_graph(b, b->cur);
+            if (st != LBM_OK) return st;
+        }
+        LBM_CUDA(b, cudaGraphLaunch(b->graph[b->cur], b->stream));
+        n -= 2;
+        b->t += 2;
+        for (lbm_ctx* c : b->box) c->t += 2;
+    }
+    if (n == 1) {
+        cudaError_t e = batch_launch_step(b, b->cur);
+        if (e != cudaSuccess) return b->fail(LBM_ECUDA, "batch step launch failed: %s", cudaGetErrorString(e));
+        b->cur ^= 1;
+        ++b->t;
+        for (lbm_ctx* c : b->box) {
+            c->cur ^= 1;
+            ++c->t;
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_tune(lbm_batch* b, int trial_steps, int* tile_y, int* zchunk, double* ms_per_step) {
+    if (!b) return LBM_EINVAL;
+    if (trial_steps < 1) return b->fail(LBM_EINVAL, "lbm_batch_tune: trial_steps must be >= 1");
+    const int tys[3] = {4, 8, 16};
+    const int zcs[4] = {8, 16, 32, 64};
+    cudaEvent_t e0, e1;
+    LBM_CUDA(b, cudaEventCreate(&e0));
+    LBM_CUDA(b, cudaEventCreate(&e1));
+    float best = -1.0f;
+    int best_ty = b->tile_y, best_zc = b->zchunk;
+    for (int ty : tys) {
+        for (int zc : zcs) {
+            if (batch_configure(b, ty, zc) != LBM_OK) continue;
+            if (batch_launch_step(b, 0) != cudaSuccess) continue;  // warm-up
+            cudaEventRecord(e0, b->stream);
+            for (int k = 0; k < trial_steps; ++k) batch_launch_step(b, k & 1);
+            cudaEventRecord(e1, b->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= trial_steps;
+            if (best < 0.0f || ms < best) {
+                best = ms;
+                best_ty = ty;
+                best_zc = zc;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return b->fail(LBM_ECUDA, "lbm_batch_tune: %s", cudaGetErrorString(e));
+    lbm_status st = batch_configure(b, best_ty, best_zc);
+    if (st != LBM_OK) return st;
+    if (tile_y) *tile_y = best_ty;
+    if (zchunk) *zchunk = best_zc;
+    if (ms_per_step) *ms_per_step = best;
+    return best < 0.0f ? b->fail(LBM_ECUDA, "lbm_batch_tune: no launch shape ran") : LBM_OK;
+}
+
+lbm_status lbm_batch_config(const lbm_batch* b, int* tile_y, int* zchunk, int* grid, long long* cells) {
+    if (!b) return LBM_EINVAL;
+    if (tile_y) *tile_y = b->tile_y;
+    if (zchunk) *zchunk = b->zchunk;
+    if (grid) *grid = b->grid;
+    if (cells) *cells = b->cells;
     return LBM_OK;
 }
 

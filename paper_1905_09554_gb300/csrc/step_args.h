@@ -24,6 +24,22 @@ struct StepArgs {
     DevParams dev;
 };
 
+// One box of a batch: geometry, work items and where its populations start
+// (element offset) in the batch's population copies.
+struct BatchBox {
+    int nx, ny, nz;
+    int tiles_x, n_tiles, zchunk;
+    int item_begin;       // first work item of the box (items are box-major)
+    long long base;       // element offset of the box's 19 population fields
+    long long n;          // cells of the box (population stride)
+};
+
+struct BatchArgs {
+    int nbox;
+    int n_items;
+    const BatchBox* boxes;  // device array of nbox entries
+};
+
 // Launch description of one step.
 struct StepLaunch {
     StepArgs args;
@@ -46,5 +62,11 @@ int prepare_step_f64(const StepLaunch& l);
 int prepare_step_f32(const StepLaunch& l);
 int prepare_step_f16(const StepLaunch& l);
 int prepare_step_bf16(const StepLaunch& l);
+
+// Batched step (pipelined kernel over many boxes; FP32 and FP64 storage).
+cudaError_t launch_batch_step_f64(const StepLaunch& l, const BatchArgs& b, const void* src, void* dst);
+cudaError_t launch_batch_step_f32(const StepLaunch& l, const BatchArgs& b, const void* src, void* dst);
+int prepare_batch_step_f64(const StepLaunch& l);
+int prepare_batch_step_f32(const StepLaunch& l);
 
 }  // namespace lbm

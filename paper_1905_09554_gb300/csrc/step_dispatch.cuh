@@ -15,10 +15,10 @@ cudaError_t launch_step_t(const StepLaunch& c, const void* src, void* dst) {
             const size_t sm = PipeLayout<Codec, TX, TY>::bytes;
             if (c.idx32)
                 sc_step_pipe_kernel<Codec, COLL, TX, TY, int><<<c.grid, TX * TY, sm, c.stream>>>(
-                    static_cast<const typename Codec::S*>(src), static_cast<typename Codec::S*>(dst), a);
+                    static_cast<const typename Codec::S*>(src), static_cast<typename Codec::S*>(dst), a, BatchArgs{});
             else
                 sc_step_pipe_kernel<Codec, COLL, TX, TY, long long><<<c.grid, TX * TY, sm, c.stream>>>(
-                    static_cast<const typename Codec::S*>(src), static_cast<typename Codec::S*>(dst), a);
+                    static_cast<const typename Codec::S*>(src), static_cast<typename Codec::S*>(dst), a, BatchArgs{});
             return cudaGetLastError();
         }
     }
@@ -96,6 +96,48 @@ cudaError_t launch_step_s(const StepLaunch& c, const void* src, void* dst) {
 template <class Codec>
 int prepare_async_s(const StepLaunch& c) {
     return c.coll == COLL_MRT ? prepare_async_c<Codec, COLL_MRT>(c) : prepare_async_c<Codec, COLL_SRT>(c);
+}
+
+// Batched pipelined step: one launch advances every box of the batch.
+template <class Codec, int COLL, int TY>
+cudaError_t launch_batch_t(const StepLaunch& c, const BatchArgs& b, const void* src, void* dst) {
+    constexpr int TX = 32;
+    const size_t sm = PipeLayout<Codec, TX, TY>::bytes;
+    sc_step_pipe_kernel<Codec, COLL, TX, TY, int, true><<<c.grid, TX * TY, sm, c.stream>>>(
+        static_cast<const typename Codec::S*>(src), static_cast<typename Codec::S*>(dst), c.args, b);
+    return cudaGetLastError();
+}
+
+template <class Codec, int COLL, int TY>
+int prepare_batch_t(const StepLaunch&) {
+    constexpr int TX = 32;
+    using Lay = PipeLayout<Codec, TX, TY>;
+    auto kern = sc_step_pipe_kernel<Codec, COLL, TX, TY, int, true>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes) != cudaSuccess)
+        return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, Lay::bytes) != cudaSuccess) return 0;
+    return per_sm;
+}
+
+template <class Codec>
+cudaError_t launch_batch_s(const StepLaunch& c, const BatchArgs& b, const void* src, void* dst) {
+    const bool mrt = c.coll == COLL_MRT;
+    switch (c.tile_y) {
+        case 4: return mrt ? launch_batch_t<Codec, COLL_MRT, 4>(c, b, src, dst) : launch_batch_t<Codec, COLL_SRT, 4>(c, b, src, dst);
+        case 16: return mrt ? launch_batch_t<Codec, COLL_MRT, 16>(c, b, src, dst) : launch_batch_t<Codec, COLL_SRT, 16>(c, b, src, dst);
+        default: return mrt ? launch_batch_t<Codec, COLL_MRT, 8>(c, b, src, dst) : launch_batch_t<Codec, COLL_SRT, 8>(c, b, src, dst);
+    }
+}
+
+template <class Codec>
+int prepare_batch_s(const StepLaunch& c) {
+    const bool mrt = c.coll == COLL_MRT;
+    switch (c.tile_y) {
+        case 4: return mrt ? prepare_batch_t<Codec, COLL_MRT, 4>(c) : prepare_batch_t<Codec, COLL_SRT, 4>(c);
+        case 16: return mrt ? prepare_batch_t<Codec, COLL_MRT, 16>(c) : prepare_batch_t<Codec, COLL_SRT, 16>(c);
+        default: return mrt ? prepare_batch_t<Codec, COLL_MRT, 8>(c) : prepare_batch_t<Codec, COLL_SRT, 8>(c);
+    }
 }
 
 }  // namespace lbm

@@ -9,4 +9,10 @@ cudaError_t launch_step_f64(const StepLaunch& l, const void* src, void* dst) {
 
 int prepare_step_f64(const StepLaunch& l) { return prepare_async_s<CodecF64>(l); }
 
+cudaError_t launch_batch_step_f64(const StepLaunch& l, const BatchArgs& b, const void* src, void* dst) {
+    return launch_batch_s<CodecF64>(l, b, src, dst);
+}
+
+int prepare_batch_step_f64(const StepLaunch& l) { return prepare_batch_s<CodecF64>(l); }
+
 }  // namespace lbm

@@ -526,10 +526,15 @@ struct PipeLayout {
 // so that 512 threads per SM stay resident.  I is the element-offset type:
 // int when 19 * cells fits in 31 bits (fewer registers and address
 // instructions), long long otherwise.
-template <class Codec, int COLL, int TX, int TY, class I>
+//
+// BATCH: the work items span several independent periodic boxes described by
+// b.boxes (geometry and offset of each box's populations in src/dst); the
+// physics parameters in `a` are shared.  Items are box-major, so a block
+// finds its box by a binary search over the boxes' first items.
+template <class Codec, int COLL, int TX, int TY, class I, bool BATCH = false>
 __global__ void __launch_bounds__(TX * TY, (TX * TY >= 512) ? 1 : 512 / (TX * TY))
-sc_step_pipe_kernel(const typename Codec::S* __restrict__ src, typename Codec::S* __restrict__ dst,
-                    const StepArgs a) {
+sc_step_pipe_kernel(const typename Codec::S* __restrict__ src_all, typename Codec::S* __restrict__ dst_all,
+                    const StepArgs a, const BatchArgs b) {
     using R = typename Codec::R;
     using S = typename Codec::S;
     using L = PipeLayout<Codec, TX, TY>;
@@ -541,9 +546,6 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src, typename Codec::S
 
     const int tid = threadIdx.x;
     const int lx = tid % TX, ly = tid / TX;
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const I n = I(a.n);
-    const I plane = I(nx) * I(ny);
     const R rho0 = R(a.rho0), inv_rho0 = R(a.inv_rho0);
     const DevParams dev = a.dev;
     const int my_slot = (ly + 1) * PX + (lx + 1);
@@ -556,11 +558,39 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src, typename Codec::S
         h_slot = (hy + 1) * PX + (hx + 1);
     }
 
-    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
-        const int tile = item % a.n_tiles, chunk = item / a.n_tiles;
-        const int x0 = (tile % a.tiles_x) * TX, y0 = (tile / a.tiles_x) * TY;
-        const int zs = chunk * a.zchunk;
-        const int ze = min(zs + a.zchunk, nz);
+    const int n_items = BATCH ? b.n_items : a.n_items;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        int nx, ny, nz, tiles_x, n_tiles, zchunk, local;
+        const S* src;
+        S* dst;
+        I n;
+        if constexpr (BATCH) {
+            int lo = 0, hi = b.nbox - 1;  // last box with item_begin <= item
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (b.boxes[mid].item_begin <= item) lo = mid;
+                else hi = mid - 1;
+            }
+            const BatchBox& bx = b.boxes[lo];
+            nx = bx.nx; ny = bx.ny; nz = bx.nz;
+            tiles_x = bx.tiles_x; n_tiles = bx.n_tiles; zchunk = bx.zchunk;
+            local = item - bx.item_begin;
+            src = src_all + bx.base;
+            dst = dst_all + bx.base;
+            n = I(bx.n);
+        } else {
+            nx = a.nx; ny = a.ny; nz = a.nz;
+            tiles_x = a.tiles_x; n_tiles = a.n_tiles; zchunk = a.zchunk;
+            local = item;
+            src = src_all;
+            dst = dst_all;
+            n = I(a.n);
+        }
+        const I plane = I(nx) * I(ny);
+        const int tile = local % n_tiles, chunk = local / n_tiles;
+        const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+        const int zs = chunk * zchunk;
+        const int ze = min(zs + zchunk, nz);
 
         const int gx = wrap_index(x0 + lx, nx), gy = wrap_index(y0 + ly, ny);
         const bool active = (x0 + lx < nx) && (y0 + ly < ny);

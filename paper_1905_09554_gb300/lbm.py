@@ -78,6 +78,16 @@ _SIGNATURES = {
     "lbm_params_sizeof": (ctypes.c_longlong, []),
     "lbm_kernel_config": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "lbm_batch_create": (ctypes.c_int, [ctypes.POINTER(lbm_params), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(_P)]),
+    "lbm_batch_destroy": (None, [_P]),
+    "lbm_batch_last_error": (ctypes.c_char_p, [_P]),
+    "lbm_batch_box": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
+    "lbm_batch_step": (ctypes.c_int, [_P, ctypes.c_long]),
+    "lbm_batch_tune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      _D]),
+    "lbm_batch_config": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]),
     "lbm_diag_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                         _P, _P, _P, _P, ctypes.c_int, _P]),
@@ -187,6 +197,44 @@ def lbm_device_bytes(ctx):
     return load().lbm_device_bytes(ctx)
 
 
+def lbm_batch_create(p: lbm_params, dims):
+    arr = (ctypes.c_int * (3 * len(dims)))(*[int(v) for d in dims for v in d])
+    b = _P()
+    st = load().lbm_batch_create(ctypes.byref(p), len(dims), arr, ctypes.byref(b))
+    return st, b
+
+
+def lbm_batch_destroy(b):
+    load().lbm_batch_destroy(b)
+
+
+def lbm_batch_last_error(b=None) -> str:
+    return (load().lbm_batch_last_error(b) or b"").decode()
+
+
+def lbm_batch_box(b, i):
+    v = _P()
+    st = load().lbm_batch_box(b, i, ctypes.byref(v))
+    return st, v
+
+
+def lbm_batch_step(b, n):
+    return load().lbm_batch_step(b, n)
+
+
+def lbm_batch_tune(b, trial_steps):
+    ty, zc, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    st = load().lbm_batch_tune(b, trial_steps, ctypes.byref(ty), ctypes.byref(zc), ctypes.byref(ms))
+    return st, dict(tile_y=ty.value, zchunk=zc.value, ms_per_step=ms.value)
+
+
+def lbm_batch_config(b):
+    v = [ctypes.c_int() for _ in range(3)]
+    cells = ctypes.c_longlong()
+    st = load().lbm_batch_config(b, *[ctypes.byref(x) for x in v], ctypes.byref(cells))
+    return st, dict(tile_y=v[0].value, zchunk=v[1].value, grid=v[2].value, cells=cells.value)
+
+
 def lbm_diag_noalloc(f, storage, nx, ny, nz, rho_ref, dev_scale, rho_l, rho_v, mass, mom, area_z,
                      maxrho_z, on_device, stream):
     """Allocation-free diagnostics on a caller-owned population array (see
@@ -204,6 +252,21 @@ def lbm_kernel_config(ctx):
 # ------------------------------------------------------------ object wrapper
 def _host_ptr(a: np.ndarray):
     return a.ctypes.data_as(_P)
+
+
+def _params(G=-5.5, tau=1.0, collision="srt", rates=None, storage="f32", rho0=1.0, rho_ref=1.0,
+            dev_scale=1.0, zchunk=0, tile_y=0, kernel=0):
+    p = lbm_params_default()
+    p.G, p.tau, p.rho0 = float(G), float(tau), float(rho0)
+    p.collision = COLLISION[collision]
+    if rates is not None:
+        p.has_rates = 1
+        for k, v in enumerate(rates):
+            p.s[k] = float(v)
+    p.storage = STORAGE[storage]
+    p.rho_ref, p.dev_scale = float(rho_ref), float(dev_scale)
+    p.zchunk, p.tile_y, p.kernel = int(zchunk), int(tile_y), int(kernel)
+    return p
 
 
 class Lattice:
@@ -351,3 +414,84 @@ class Lattice:
         st, cfg = lbm_kernel_config(self.ctx)
         self._check(st)
         return cfg
+
+
+class _BoxView(Lattice):
+    """Lattice-like access to one box of a Batch (no buffers of its own)."""
+
+    def __init__(self, batch, i, ctx, shape):
+        self.ctx = ctx
+        self.shape = shape
+        self.n = shape[0] * shape[1] * shape[2]
+        self._bufs = None
+        self._batch = batch
+        self.index = i
+
+    def close(self):
+        self.ctx = None  # owned by the batch
+
+    def step(self, n=1):
+        raise LbmError(LBM_EINVAL, "boxes of a batch are stepped together with Batch.step")
+
+
+class Batch:
+    """Independent periodic boxes (dims: list of (nx, ny, nz)) advanced
+    together; the physics keywords are those of Lattice (FP32/FP64 only)."""
+
+    def __init__(self, dims, stream=None, **kw):
+        load()
+        p = _params(**kw)
+        if stream is not None:
+            p.stream = int(stream)
+        else:
+            import torch
+            if torch.cuda.is_available():
+                s = torch.cuda.current_stream().cuda_stream
+                p.stream = s if s else None
+        st, b = lbm_batch_create(p, dims)
+        if st != LBM_OK:
+            raise LbmError(st, lbm_batch_last_error(None))
+        self.b = b
+        self.dims = [tuple(int(v) for v in d) for d in dims]
+        self.boxes = []
+        for i, (nx, ny, nz) in enumerate(self.dims):
+            st, v = lbm_batch_box(b, i)
+            self._check(st)
+            self.boxes.append(_BoxView(self, i, v, (nz, ny, nx)))
+
+    def _check(self, st):
+        if st != LBM_OK:
+            raise LbmError(st, lbm_batch_last_error(self.b))
+
+    def step(self, n=1):
+        self._check(lbm_batch_step(self.b, int(n)))
+
+    def tune(self, trial_steps=3):
+        st, r = lbm_batch_tune(self.b, int(trial_steps))
+        self._check(st)
+        return r
+
+    def config(self):
+        st, r = lbm_batch_config(self.b)
+        self._check(st)
+        return r
+
+    def close(self):
+        if getattr(self, "b", None):
+            for v in self.boxes:
+                v.ctx = None
+            lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
