@@ -165,6 +165,32 @@ lbm_status lbm_kernel_config(const lbm_ctx *ctx, int *kernel, int *tile_y,
 long long lbm_params_sizeof(void);
 
 /* ---------------------------------------------------------------------------
+ * Discrete adjoint of the SRT step (Sec. 2: Eqs. LBE, local_eq, momentum,
+ * SC_force, vel_shift), for gradients of an objective J(rho(T)) with respect
+ * to the initial density, G and tau.  Not in the paper: a GPU service built on
+ * its step.  FP32 or FP64 storage (the adjoint field uses the storage type,
+ * the G and tau gradients are summed in float64).
+ * ------------------------------------------------------------------------- */
+
+/* Start from rest with density rho0 (host or device, float64, nx*ny*nz), run
+ * n >= 1 steps and keep every `every`-th state (t = 0, every, 2 every, ...) as
+ * a checkpoint in device memory owned by the context; the state ends at
+ * t = n.  Checkpoint memory: ceil(n/every) + every states.  Collision must be
+ * LBM_SRT_SHIFT (else LBM_EUNSUPPORTED). */
+lbm_status lbm_adjoint_forward(lbm_ctx *ctx, const double *rho0, int on_device,
+                               long n, int every);
+
+/* Given dJdrho = dJ/drho(x, T) (float64 field, host or device), run the
+ * discrete adjoint back to t = 0, recomputing each segment's states from its
+ * checkpoint, and return dJ/drho0 (float64 field, host or device; may be
+ * NULL), dJ/dG and dJ/dtau (host doubles; may be NULL).  Synchronises the
+ * context's stream. */
+lbm_status lbm_adjoint_backward(lbm_ctx *ctx, const double *dJdrho,
+                                int in_on_device, double *dJdrho0,
+                                int out_on_device, double *dJdG,
+                                double *dJdtau);
+
+/* ---------------------------------------------------------------------------
  * Batches: many independent periodic boxes (uneven sizes) advanced together.
  * The method is the paper's step (Sec. 2) applied to each box; batching is a
  * GPU execution form, not in the paper.

@@ -1,0 +1,260 @@
+// Discrete adjoint of the SRT Shan-Chen step (Sec. 2: Eqs. LBE, local_eq,
+// momentum, SC_force, vel_shift), for FP32 or FP64 populations.
+//
+// Forward step at time t (state f = post-streaming populations):
+//   rho = sum f, j = sum c f, psi = psi(rho), S(x) = sum_a w_a psi(x + c_a) c_a,
+//   F = -G psi S, u' = (j + tau F)/rho, f* = f + omega (f_eq(rho, u') - f),
+//   f_a(x + c_a, t + 1) = f*_a(x).
+// Reverse step, given lam(t+1) = dJ/df(t+1):
+//   1. streaming adjoint (pull): lam*_a(x) = lam_a(x + c_a, t+1);
+//   2. collision adjoint (local, adj_collide_kernel): lam_loc = (df*/df)^T lam*,
+//      gF = (df*/dF)^T lam*, and the tau and G terms of the parameter
+//      gradients;
+//   3. force adjoint (a gather over neighbours, adj_force_kernel):
+//      g_psi(y) = -G [ S(y).gF(y) + sum_a w_a psi(y - c_a) c_a . gF(y - c_a) ],
+//      g_rho = g_psi psi'(rho) with psi' = exp(-rho/rho0) = 1 - psi/rho0,
+//      lam_a(y, t) = lam_loc_a(y) + g_rho(y) for every a.
+// Parameter gradients are summed in float64 per block and reduced in a fixed
+// order (deterministic).
+#include <cuda_runtime.h>
+
+#include "adjoint.h"
+#include "lattice.cuh"
+
+namespace lbm {
+namespace {
+
+constexpr int kThreads = 256;
+
+struct Cell {
+    int x, y, z;
+};
+
+__device__ __forceinline__ Cell cell_of(long long i, int nx, int ny) {
+    Cell c;
+    c.x = int(i % nx);
+    c.y = int((i / nx) % ny);
+    c.z = int(i / ((long long)nx * ny));
+    return c;
+}
+
+// Index of x + (dx, dy, dz), periodic (|d| <= 1).
+__device__ __forceinline__ long long shifted(const Cell& c, int dx, int dy, int dz, int nx, int ny, int nz) {
+    int xx = c.x + dx, yy = c.y + dy, zz = c.z + dz;
+    xx = xx < 0 ? nx - 1 : (xx == nx ? 0 : xx);
+    yy = yy < 0 ? ny - 1 : (yy == ny ? 0 : yy);
+    zz = zz < 0 ? nz - 1 : (zz == nz ? 0 : zz);
+    return ((long long)zz * ny + yy) * nx + xx;
+}
+
+template <class R>
+__device__ __forceinline__ R psi_fn(R rho, R rho0) {
+    return rho0 * (R(1) - exp(-rho / rho0));
+}
+
+template <class R>
+__global__ void __launch_bounds__(kThreads) adj_psi_kernel(const R* __restrict__ f, R* __restrict__ psi, long long n,
+                                                           R rho0) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        R r = R(0);
+        static_for<0, Q>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            r += f[q * n + i];
+        });
+        psi[i] = psi_fn<R>(r, rho0);
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void block_sum2(double a, double b, double* out2) {
+    __shared__ double red[2][kThreads];
+    red[0][threadIdx.x] = a;
+    red[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + s];
+            red[1][threadIdx.x] += red[1][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out2[0] = red[0][0];
+        out2[1] = red[1][0];
+    }
+}
+
+template <class R>
+__global__ void __launch_bounds__(kThreads)
+adj_collide_kernel(const R* __restrict__ f, const R* __restrict__ psi, const R* __restrict__ lam_next,
+                   R* __restrict__ lam_out, R* __restrict__ gF, double* __restrict__ partials, AdjointArgs a) {
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const long long n = a.n;
+    const R G = R(a.G), tau = R(a.tau), omega = R(a.omega);
+    double accG = 0.0, accT = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const Cell c = cell_of(i, nx, ny);
+        R fv[Q], ls[Q];
+        R rho = R(0), jx = R(0), jy = R(0), jz = R(0), sx = R(0), sy = R(0), sz = R(0);
+        static_for<0, Q>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            fv[q] = f[q * n + i];
+            rho += fv[q];
+            jx += R(cx(q)) * fv[q];
+            jy += R(cy(q)) * fv[q];
+            jz += R(cz(q)) * fv[q];
+            const long long nb = shifted(c, cx(q), cy(q), cz(q), nx, ny, nz);
+            ls[q] = lam_next[q * n + nb];  // streaming adjoint: pull from x + c_q
+            if constexpr (q != 0) {
+                const R pn = psi[nb];
+                sx += R(wq(q) * cx(q)) * pn;
+                sy += R(wq(q) * cy(q)) * pn;
+                sz += R(wq(q) * cz(q)) * pn;
+            }
+        });
+        const R ps = psi[i];
+        const R Fx = -G * ps * sx, Fy = -G * ps * sy, Fz = -G * ps * sz;
+        const R inv_rho = R(1) / rho;
+        const R ux = (jx + tau * Fx) * inv_rho, uy = (jy + tau * Fy) * inv_rho, uz = (jz + tau * Fz) * inv_rho;
+        const R u2 = ux * ux + uy * uy + uz * uz;
+        // adjoint of f* = (1 - omega) f + omega f_eq(rho, u')
+        R g_rho = R(0), gux = R(0), guy = R(0), guz = R(0), g_tau = R(0);
+        static_for<0, Q>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            const R cu = R(cx(q)) * ux + R(cy(q)) * uy + R(cz(q)) * uz;
+            const R wr = R(wq(q)) * rho;
+            const R feq = wr * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * u2);
+            const R mu = omega * ls[q];
+            g_rho += mu * feq * inv_rho;
+            // d f_eq / d u' = w rho (3 c + 9 (c.u') c - 3 u')
+            const R k = R(3) + R(9) * cu;
+            gux += mu * wr * (k * R(cx(q)) - R(3) * ux);
+            guy += mu * wr * (k * R(cy(q)) - R(3) * uy);
+            guz += mu * wr * (k * R(cz(q)) - R(3) * uz);
+            g_tau -= ls[q] * (feq - fv[q]) * (omega * omega);  // d omega / d tau = -1/tau^2
+        });
+        // u' = (j + tau F)/rho
+        const R gjx = gux * inv_rho, gjy = guy * inv_rho, gjz = guz * inv_rho;
+        g_rho -= (gux * ux + guy * uy + guz * uz) * inv_rho;
+        g_tau += (gux * Fx + guy * Fy + guz * Fz) * inv_rho;
+        const R gFx = tau * gjx, gFy = tau * gjy, gFz = tau * gjz;
+        static_for<0, Q>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            lam_out[q * n + i] = (R(1) - omega) * ls[q] + g_rho + R(cx(q)) * gjx + R(cy(q)) * gjy + R(cz(q)) * gjz;
+        });
+        gF[i] = gFx;
+        gF[n + i] = gFy;
+        gF[2 * n + i] = gFz;
+        // dF/dG = -psi S
+        accG += double(-(ps * sx) * gFx - (ps * sy) * gFy - (ps * sz) * gFz);
+        accT += double(g_tau);
+    }
+    block_sum2<R>(accG, accT, partials + 2 * blockIdx.x);
+}
+
+template <class R>
+__global__ void __launch_bounds__(kThreads)
+adj_force_kernel(const R* __restrict__ psi, const R* __restrict__ gF, R* __restrict__ lam, AdjointArgs a) {
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const long long n = a.n;
+    const R G = R(a.G), rho0 = R(a.rho0);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const Cell c = cell_of(i, nx, ny);
+        R term = R(0);
+        R sx = R(0), sy = R(0), sz = R(0);
+        static_for<1, Q>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            const long long up = shifted(c, cx(q), cy(q), cz(q), nx, ny, nz);     // y + c_q
+            const long long dn = shifted(c, -cx(q), -cy(q), -cz(q), nx, ny, nz);  // y - c_q
+            const R pu = psi[up];
+            sx += R(wq(q) * cx(q)) * pu;
+            sy += R(wq(q) * cy(q)) * pu;
+            sz += R(wq(q) * cz(q)) * pu;
+            const R pd = psi[dn] * R(wq(q));
+            term += pd * (R(cx(q)) * gF[dn] + R(cy(q)) * gF[n + dn] + R(cz(q)) * gF[2 * n + dn]);
+        });
+        term += sx * gF[i] + sy * gF[n + i] + sz * gF[2 * n + i];
+        const R ps = psi[i];
+        const R g_rho = -G * term * (R(1) - ps / rho0);
+        static_for<0, Q>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            lam[q * n + i] += g_rho;
+        });
+    }
+}
+
+// lam_a(x, T) = dJ/drho(x) for every a (rho = sum_a f_a).
+template <class R>
+__global__ void adj_seed_kernel(const double* __restrict__ g, R* __restrict__ lam, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const R v = R(g[i]);
+        static_for<0, Q>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            lam[q * n + i] = v;
+        });
+    }
+}
+
+// f_a(x, 0) = w_a rho0(x): dJ/drho0(x) = sum_a w_a lam_a(x, 0).
+template <class R>
+__global__ void adj_rho0_kernel(const R* __restrict__ lam, double* __restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        static_for<0, Q>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            s += wq(q) * double(lam[q * n + i]);
+        });
+        out[i] = s;
+    }
+}
+
+// Fixed-order sum of the per-block partials into acc[0..1].
+__global__ void adj_reduce_kernel(const double* __restrict__ partials, int nblocks, double* __restrict__ acc) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double g = 0.0, t = 0.0;
+        for (int b = 0; b < nblocks; ++b) {
+            g += partials[2 * b];
+            t += partials[2 * b + 1];
+        }
+        acc[0] += g;
+        acc[1] += t;
+    }
+}
+
+template <class R>
+cudaError_t run_adjoint_step(const AdjointArgs& a, const void* f, void* psi, const void* lam_next, void* lam_out,
+                             void* gF, double* partials, double* acc, cudaStream_t st) {
+    const int grid = a.grid;
+    adj_psi_kernel<R><<<grid, kThreads, 0, st>>>(static_cast<const R*>(f), static_cast<R*>(psi), a.n, R(a.rho0));
+    adj_collide_kernel<R><<<grid, kThreads, 0, st>>>(static_cast<const R*>(f), static_cast<const R*>(psi),
+                                                     static_cast<const R*>(lam_next), static_cast<R*>(lam_out),
+                                                     static_cast<R*>(gF), partials, a);
+    adj_force_kernel<R><<<grid, kThreads, 0, st>>>(static_cast<const R*>(psi), static_cast<const R*>(gF),
+                                                   static_cast<R*>(lam_out), a);
+    adj_reduce_kernel<<<1, 32, 0, st>>>(partials, grid, acc);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t adjoint_step(const AdjointArgs& a, bool f64, const void* f, void* psi, const void* lam_next,
+                         void* lam_out, void* gF, double* partials, double* acc, cudaStream_t st) {
+    return f64 ? run_adjoint_step<double>(a, f, psi, lam_next, lam_out, gF, partials, acc, st)
+               : run_adjoint_step<float>(a, f, psi, lam_next, lam_out, gF, partials, acc, st);
+}
+
+cudaError_t adjoint_seed(const AdjointArgs& a, bool f64, const double* dJdrho, void* lam, cudaStream_t st) {
+    if (f64) adj_seed_kernel<double><<<a.grid, kThreads, 0, st>>>(dJdrho, static_cast<double*>(lam), a.n);
+    else adj_seed_kernel<float><<<a.grid, kThreads, 0, st>>>(dJdrho, static_cast<float*>(lam), a.n);
+    return cudaGetLastError();
+}
+
+cudaError_t adjoint_rho0(const AdjointArgs& a, bool f64, const void* lam, double* out, cudaStream_t st) {
+    if (f64) adj_rho0_kernel<double><<<a.grid, kThreads, 0, st>>>(static_cast<const double*>(lam), out, a.n);
+    else adj_rho0_kernel<float><<<a.grid, kThreads, 0, st>>>(static_cast<const float*>(lam), out, a.n);
+    return cudaGetLastError();
+}
+
+int adjoint_threads() { return kThreads; }
+
+}  // namespace lbm

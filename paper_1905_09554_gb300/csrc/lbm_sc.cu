@@ -16,6 +16,7 @@
 #include "diag_cell.cuh"
 #include "lattice.cuh"
 #include "step_args.h"
+#include "adjoint.h"
 
 using namespace lbm;
 
@@ -44,6 +45,20 @@ struct lbm_ctx {
     bool idx32 = false;               // 19 * cells fits 32-bit element offsets
     char err[512] = {0};
     lbm_batch* batch = nullptr;       // set when the context is a view of a batch box
+    // discrete adjoint (allocated by lbm_adjoint_forward)
+    struct Adjoint {
+        void* cp = nullptr;           // checkpoints, ncp states
+        void* seg = nullptr;          // recomputed states of one segment, `every` states
+        void* lam[2] = {nullptr, nullptr};
+        void* psi = nullptr;
+        void* gF = nullptr;
+        double* partials = nullptr;   // 2 per block
+        double* acc = nullptr;        // dJ/dG, dJ/dtau
+        double* io = nullptr;         // host <-> device staging of one field
+        size_t cp_bytes = 0, seg_bytes = 0;
+        long T = -1;                  // steps of the recorded forward run
+        int every = 0, ncp = 0;
+    } adj;
 
     lbm_status fail(lbm_status s, const char* fmt, ...) {
         va_list ap;
@@ -512,6 +527,15 @@ void lbm_destroy(lbm_ctx* c) {
     }
     cudaFree(c->scratch);
     cudaFree(c->diag);
+    cudaFree(c->adj.cp);
+    cudaFree(c->adj.seg);
+    cudaFree(c->adj.lam[0]);
+    cudaFree(c->adj.lam[1]);
+    cudaFree(c->adj.psi);
+    cudaFree(c->adj.gF);
+    cudaFree(c->adj.partials);
+    cudaFree(c->adj.acc);
+    cudaFree(c->adj.io);
     delete c;
 }
 
@@ -1050,6 +1074,150 @@ lbm_status lbm_batch_config(const lbm_batch* b, int* tile_y, int* zchunk, int* g
     if (zchunk) *zchunk = b->zchunk;
     if (grid) *grid = b->grid;
     if (cells) *cells = b->cells;
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------------------
+// Discrete adjoint (SRT)
+// ----------------------------------------------------------------------------
+namespace {
+
+AdjointArgs adjoint_args(const lbm_ctx* c) {
+    AdjointArgs a;
+    a.nx = c->p.nx;
+    a.ny = c->p.ny;
+    a.nz = c->p.nz;
+    a.n = c->n;
+    a.G = c->p.G;
+    a.tau = c->p.tau;
+    a.omega = 1.0 / c->p.tau;
+    a.rho0 = c->p.rho0;
+    const long long want = (c->n + adjoint_threads() - 1) / adjoint_threads();
+    const long long cap = 8LL * c->num_sms;
+    a.grid = int(want < cap ? (want < 1 ? 1 : want) : cap);
+    return a;
+}
+
+lbm_status adj_alloc(lbm_ctx* c, void** p, size_t bytes) {
+    if (*p) return LBM_OK;
+    LBM_CUDA(c, cudaMalloc(p, bytes));
+    c->own_bytes += (long long)bytes;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_adjoint_forward(lbm_ctx* c, const double* rho0, int on_device, long nsteps, int every) {
+    if (!c) return LBM_EINVAL;
+    if (c->batch) return c->fail(LBM_EINVAL, "lbm_adjoint_forward: not available on a batch box");
+    if (c->p.collision != LBM_SRT_SHIFT)
+        return c->fail(LBM_EUNSUPPORTED, "lbm_adjoint_forward: the adjoint covers the SRT operator only");
+    if (c->p.storage != LBM_F32 && c->p.storage != LBM_F64)
+        return c->fail(LBM_EUNSUPPORTED, "lbm_adjoint_forward: FP32 or FP64 storage only");
+    if (!rho0 || nsteps < 1 || every < 1) return c->fail(LBM_EINVAL, "lbm_adjoint_forward: need rho0, n >= 1, every >= 1");
+    auto& A = c->adj;
+    const size_t state = (size_t)Q * (size_t)c->n * c->elem;
+    const int ncp = int((nsteps + every - 1) / every);
+    if (A.cp && (A.cp_bytes < (size_t)ncp * state)) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(A.cp);
+        c->own_bytes -= (long long)A.cp_bytes;
+        A.cp = nullptr;
+    }
+    if (A.seg && (A.seg_bytes < (size_t)every * state)) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(A.seg);
+        c->own_bytes -= (long long)A.seg_bytes;
+        A.seg = nullptr;
+    }
+    if (!A.cp) {
+        lbm_status st = adj_alloc(c, &A.cp, (size_t)ncp * state);
+        if (st != LBM_OK) return st;
+        A.cp_bytes = (size_t)ncp * state;
+    }
+    if (!A.seg) {
+        lbm_status st = adj_alloc(c, &A.seg, (size_t)every * state);
+        if (st != LBM_OK) return st;
+        A.seg_bytes = (size_t)every * state;
+    }
+    lbm_status st = lbm_set_density(c, rho0, on_device);
+    if (st != LBM_OK) return st;
+    for (long t = 0; t < nsteps; ++t) {
+        if (t % every == 0)
+            LBM_CUDA(c, cudaMemcpyAsync(static_cast<char*>(A.cp) + (size_t)(t / every) * state, c->f[c->cur], state,
+                                        cudaMemcpyDeviceToDevice, c->stream));
+        st = lbm_step(c, 1);
+        if (st != LBM_OK) return st;
+    }
+    A.T = nsteps;
+    A.every = every;
+    A.ncp = ncp;
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint_backward(lbm_ctx* c, const double* dJdrho, int in_on_device, double* dJdrho0,
+                                int out_on_device, double* dJdG, double* dJdtau) {
+    if (!c) return LBM_EINVAL;
+    auto& A = c->adj;
+    if (A.T < 1) return c->fail(LBM_EINVAL, "lbm_adjoint_backward: call lbm_adjoint_forward first");
+    if (!dJdrho) return c->fail(LBM_EINVAL, "lbm_adjoint_backward: dJdrho is NULL");
+    const bool f64 = c->p.storage == LBM_F64;
+    const size_t state = (size_t)Q * (size_t)c->n * c->elem;
+    const AdjointArgs a = adjoint_args(c);
+    lbm_status st;
+    for (void** p : {&A.lam[0], &A.lam[1]}) {
+        st = adj_alloc(c, p, state);
+        if (st != LBM_OK) return st;
+    }
+    if ((st = adj_alloc(c, &A.psi, (size_t)c->n * c->elem)) != LBM_OK) return st;
+    if ((st = adj_alloc(c, &A.gF, 3 * (size_t)c->n * c->elem)) != LBM_OK) return st;
+    if ((st = adj_alloc(c, reinterpret_cast<void**>(&A.partials), sizeof(double) * 2 * (size_t)a.grid)) != LBM_OK)
+        return st;
+    if ((st = adj_alloc(c, reinterpret_cast<void**>(&A.acc), sizeof(double) * 2)) != LBM_OK) return st;
+    if ((!in_on_device || (dJdrho0 && !out_on_device)) &&
+        (st = adj_alloc(c, reinterpret_cast<void**>(&A.io), sizeof(double) * (size_t)c->n)) != LBM_OK)
+        return st;
+    const double* g = dJdrho;
+    if (!in_on_device) {
+        LBM_CUDA(c, cudaMemcpyAsync(A.io, dJdrho, sizeof(double) * (size_t)c->n, cudaMemcpyHostToDevice, c->stream));
+        g = A.io;
+    }
+    LBM_CUDA(c, cudaMemsetAsync(A.acc, 0, 2 * sizeof(double), c->stream));
+    LBM_CUDA(c, adjoint_seed(a, f64, g, A.lam[0], c->stream));
+    int cur = 0;  // lam[cur] holds dJ/df(t+1)
+    for (int k = A.ncp - 1; k >= 0; --k) {
+        const long t0 = (long)k * A.every;
+        const long t1 = t0 + A.every < A.T ? t0 + A.every : A.T;
+        // recompute the segment's states from its checkpoint
+        char* seg = static_cast<char*>(A.seg);
+        LBM_CUDA(c, cudaMemcpyAsync(seg, static_cast<char*>(A.cp) + (size_t)k * state, state,
+                                    cudaMemcpyDeviceToDevice, c->stream));
+        for (long t = t0; t + 1 < t1; ++t) {
+            cudaError_t e = launch_step(c, seg + (size_t)(t - t0) * state, seg + (size_t)(t - t0 + 1) * state);
+            if (e != cudaSuccess) return c->fail(LBM_ECUDA, "adjoint recompute: %s", cudaGetErrorString(e));
+        }
+        for (long t = t1 - 1; t >= t0; --t) {
+            cudaError_t e = adjoint_step(a, f64, seg + (size_t)(t - t0) * state, A.psi, A.lam[cur], A.lam[cur ^ 1],
+                                         A.gF, A.partials, A.acc, c->stream);
+            if (e != cudaSuccess) return c->fail(LBM_ECUDA, "adjoint step: %s", cudaGetErrorString(e));
+            cur ^= 1;
+        }
+    }
+    if (dJdrho0) {
+        double* out = out_on_device ? dJdrho0 : A.io;
+        LBM_CUDA(c, adjoint_rho0(a, f64, A.lam[cur], out, c->stream));
+        if (!out_on_device)
+            LBM_CUDA(c, cudaMemcpyAsync(dJdrho0, A.io, sizeof(double) * (size_t)c->n, cudaMemcpyDeviceToHost, c->stream));
+    }
+    double acc[2] = {0.0, 0.0};
+    LBM_CUDA(c, cudaMemcpyAsync(acc, A.acc, sizeof(acc), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (dJdG) *dJdG = acc[0];
+    if (dJdtau) *dJdtau = acc[1];
     return LBM_OK;
 }
 

@@ -88,6 +88,8 @@ _SIGNATURES = {
                                       _D]),
     "lbm_batch_config": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]),
+    "lbm_adjoint_forward": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_long, ctypes.c_int]),
+    "lbm_adjoint_backward": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int, _D, _D]),
     "lbm_diag_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                         _P, _P, _P, _P, ctypes.c_int, _P]),
@@ -195,6 +197,14 @@ def lbm_set_stream(ctx, stream):
 
 def lbm_device_bytes(ctx):
     return load().lbm_device_bytes(ctx)
+
+
+def lbm_adjoint_forward(ctx, rho0, on_device, n, every):
+    return load().lbm_adjoint_forward(ctx, rho0, on_device, n, every)
+
+
+def lbm_adjoint_backward(ctx, dJdrho, in_on_device, dJdrho0, out_on_device, dJdG, dJdtau):
+    return load().lbm_adjoint_backward(ctx, dJdrho, in_on_device, dJdrho0, out_on_device, dJdG, dJdtau)
 
 
 def lbm_batch_create(p: lbm_params, dims):
@@ -409,6 +419,33 @@ class Lattice:
 
     def device_bytes(self):
         return lbm_device_bytes(self.ctx)
+
+    def adjoint_forward(self, rho0, n, every):
+        """Run n steps from rest with density rho0 keeping checkpoints."""
+        if isinstance(rho0, np.ndarray):
+            a = np.ascontiguousarray(rho0, dtype=np.float64)
+            self._check(lbm_adjoint_forward(self.ctx, _host_ptr(a), 0, int(n), int(every)))
+        else:
+            assert rho0.is_cuda and rho0.is_contiguous() and rho0.numel() == self.n
+            self._check(lbm_adjoint_forward(self.ctx, rho0.data_ptr(), 1, int(n), int(every)))
+
+    def adjoint_backward(self, dJdrho, out=None):
+        """Returns (dJ/drho0, dJ/dG, dJ/dtau); dJdrho and out may be numpy
+        arrays or CUDA float64 tensors."""
+        dG, dT = ctypes.c_double(), ctypes.c_double()
+        if isinstance(dJdrho, np.ndarray):
+            g = np.ascontiguousarray(dJdrho, dtype=np.float64)
+            gp, gdev = _host_ptr(g), 0
+        else:
+            assert dJdrho.is_cuda and dJdrho.is_contiguous()
+            gp, gdev = dJdrho.data_ptr(), 1
+        if out is None:
+            res = np.empty(self.shape)
+            op, odev = _host_ptr(res), 0
+        else:
+            res, op, odev = out, out.data_ptr(), 1
+        self._check(lbm_adjoint_backward(self.ctx, gp, gdev, op, odev, ctypes.byref(dG), ctypes.byref(dT)))
+        return res, dG.value, dT.value
 
     def kernel_config(self):
         st, cfg = lbm_kernel_config(self.ctx)
