@@ -25,6 +25,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -57,8 +58,12 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", choices=["single", "batched"], default="single",
-                    help="single: the sharp-interface ligament; batched: 64 uneven ligaments in one launch per step")
+    ap.add_argument("--form", choices=["single", "batched", "adjoint", "precision"], default="single",
+                    help="single: the sharp-interface ligament; batched: 64 uneven ligaments in one launch per "
+                         "step; adjoint: gradients of the neck energy through 500 steps; precision: FP32/FP16/BF16 "
+                         "storage against FP64")
+    ap.add_argument("--breakup-R0", type=float, default=32.0,
+                    help="precision form: ligament radius of the run-to-break-up comparison")
     return ap.parse_args()
 
 
@@ -183,6 +188,26 @@ def run_reference(args):
     }), flush=True)
 
 
+# --------------------------------------------------------------- multi-rank
+def max_over_ranks(x, dist=None):
+    """Maximum of a per-rank float over all ranks (NCCL: on the rank's GPU;
+    gloo: on the host).  With no process group, x itself."""
+    if dist is None or not dist.is_initialized():
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(cells_per_rank, steps, max_ms, world):
+    """MLUPS of the whole job: every rank advances its own replica of
+    cells_per_rank cells by `steps` steps; the job takes the slowest rank's
+    time."""
+    return world * cells_per_rank * steps / (max_ms / 1e3) / 1e6
+
+
 # ------------------------------------------------------------------- GPU arm
 def run_ours(args):
     import numpy as np
@@ -243,11 +268,8 @@ def run_ours(args):
     d1 = L.diag(w["rho_l"], w["rho_v"])
     mass_drift = abs(d1["mass"] - d0["mass"]) / d0["mass"]
 
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * ncell * args.steps / (total_ms / 1e3) / 1e6
+    total_ms = max_over_ranks(total_ms, dist)
+    value = whole_job_mlups(ncell, args.steps, total_ms, world)
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -268,10 +290,7 @@ def run_ours(args):
         lbm.lbm_moments(L.ctx, rho_out.data_ptr(), None, None, None, 0)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(dt, dist)
         n_diag = (K + diag_every - 1) // diag_every
         e2e = {"value": world * ncell * K / dt / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": 8 * ncell / K,
@@ -389,12 +408,155 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def golden_sigma(forcing):
+    path = os.path.join(ROOT, "tests", "golden", "sigma.json")
+    try:
+        with open(path) as fh:
+            return [c for c in json.load(fh)["cases"] if c["forcing"] == forcing][0]["sigma"]
+    except Exception:
+        return None
+
+
+def run_adjoint(args):
+    """Gradient of the neck energy J = mean_z (R(z) - mean R)^2 at step 500 with
+    respect to the initial density, G and tau, for the 64 x 64 x 180 ligament
+    (R0 = 16, kR0 = 0.56, 5% perturbation plus N(0, 1e-3) per-cell noise from
+    seed 1), SRT tau = 1, G = -5.5, FP32 populations, checkpoints every 23
+    steps.  `value` is adjoint steps/s of the backward pass (which includes
+    recomputing each segment from its checkpoint); the FP64 gradient of the
+    same problem is the accuracy reference."""
+    import numpy as np
+    import torch
+
+    from paper_1905_09554_gb300 import inputs, lbm
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    nx, ny, nz = 64, 64, 180
+    R0, T, every = 16.0, 500, 23
+    rl, rv = inputs.COEXISTENCE[("shift", -5.5, 1.0)]
+    rho0 = inputs.noisy_ligament_density(nx, ny, nz, R0, 0.05, rl, rv, 1e-3, seed=1)
+
+    def dJ(rho):
+        A = ((rho - rv) / (rl - rv)).sum(axis=(1, 2))
+        R = np.sqrt(A / np.pi)
+        g = (2.0 / nz) * (R - R.mean()) / (2.0 * np.pi * R * (rl - rv))
+        return np.broadcast_to(g[:, None, None], rho.shape).copy(), float(((R - R.mean()) ** 2).mean())
+
+    out = {}
+    for storage in ("f32", "f64"):
+        with lbm.Lattice(nx, ny, nz, G=-5.5, tau=1.0, storage=storage) as L:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            L.adjoint_forward(rho0, T, every)
+            r, _ = L.moments()
+            t1 = time.perf_counter()
+            g, J = dJ(r)
+            t2 = time.perf_counter()
+            grad, gG, gT = L.adjoint_backward(g)
+            t3 = time.perf_counter()
+        out[storage] = dict(J=J, grad=grad, dG=gG, dtau=gT, fwd_s=t1 - t0, bwd_s=t3 - t2)
+    a, b = out["f32"], out["f64"]
+    line = {
+        "metric": "adjoint steps/s (SRT, 64x64x180, 500 steps, checkpoints every 23)",
+        "value": T / a["bwd_s"], "unit": "adjoint steps/s", "n_gpus": 1, "steps": T, "warmup": 0,
+        "ms_per_step": a["bwd_s"] / T * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "ligament 64x64x180, R0=16, kR0=0.56, 5% perturbation + N(0,1e-3) noise seed 1, "
+                               "G=-5.5, SRT tau=1, objective: neck energy at step 500",
+                   "checkpoint_every": every, "cells": nx * ny * nz},
+        "forward_with_checkpoints_steps_per_s": T / a["fwd_s"],
+        "fp64": {"adjoint_steps_per_s": T / b["bwd_s"], "dJ_dG": b["dG"], "dJ_dtau": b["dtau"], "J": b["J"]},
+        "fp32": {"dJ_dG": a["dG"], "dJ_dtau": a["dtau"], "J": a["J"]},
+        "fp32_vs_fp64": {"dJ_dG_rel": abs(a["dG"] - b["dG"]) / abs(b["dG"]),
+                         "dJ_dtau_rel": abs(a["dtau"] - b["dtau"]) / abs(b["dtau"]),
+                         "dJ_drho0_maxabs_rel": float(np.abs(a["grad"] - b["grad"]).max() / np.abs(b["grad"]).max())},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_precision(args):
+    """Population storage formats against the FP64 run (MRT, G = -5.5,
+    tau = 1, shear rule): max-abs rho and u error after 200 steps of the
+    R0 = --R0 ligament (kR0 = 0.7, 5% perturbation), and the growth rate and
+    break-up time of the R0 = --breakup-R0 ligament run to break-up."""
+    import numpy as np
+    import torch
+
+    from paper_1905_09554_gb300 import diagnostics as dg
+    from paper_1905_09554_gb300 import inputs, lbm
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rl, rv = inputs.COEXISTENCE[("guo", -5.5, 1.0)]
+    rates = [1.0] * 19  # shear rule at tau = 1: every rate is 1
+    sig = golden_sigma("guo")
+    fmts = ["f64", "f32", "f16", "bf16"]
+    res = {f: {} for f in fmts}
+    nx, ny, nz = inputs.ligament_box(args.R0, args.kR0)
+    fields = {}
+    for f in fmts:
+        with lbm.Lattice(nx, ny, nz, G=-5.5, tau=1.0, collision="mrt", rates=rates, storage=f) as L:
+            L.init_ligament(args.R0, 0.05, rl, rv)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            L.step(200)
+            torch.cuda.synchronize()
+            res[f]["mlups_200"] = nx * ny * nz * 200 / (time.perf_counter() - t0) / 1e6
+            fields[f] = L.moments()
+    for f in fmts[1:]:
+        res[f]["err200_rho"] = float(np.abs(fields[f][0] - fields["f64"][0]).max())
+        res[f]["err200_u"] = float(np.abs(fields[f][1] - fields["f64"][1]).max())
+    del fields
+    R0b = args.breakup_R0
+    bx, by, bz = inputs.ligament_box(R0b, args.kR0)
+    tcap = math.sqrt(rl * R0b ** 3 / sig) if sig else 1000.0
+    every = 20
+    for f in fmts:
+        with lbm.Lattice(bx, by, bz, G=-5.5, tau=1.0, collision="mrt", rates=rates, storage=f) as L:
+            L.init_ligament(R0b, 0.05, rl, rv)
+            ts, amps, mins = [], [], []
+            t = 0
+            while t <= 60 * tcap:
+                d = L.diag(rl, rv, raise_nonfinite=False)
+                ts.append(t)
+                amps.append(dg.mode_amplitude(d["area_z"]))
+                mins.append(float(d["maxrho_z"].min()))
+                if mins[-1] < 0.5 * (rl + rv) or d["status"] != 0:
+                    break
+                L.step(every)
+                t += every
+        tb = dg.breakup_time(ts, mins, rl, rv)
+        w = dg.growth_rate(ts, amps, t_start=tcap, a_stop=0.3 * R0b)
+        res[f]["t_break"] = tb
+        res[f]["t_break_over_tcap"] = tb / tcap if tb is not None else None
+        res[f]["growth_rate_x_tcap"] = w * tcap if w is not None else None
+    for f in fmts[1:]:
+        ref = res["f64"]
+        res[f]["t_break_rel_err"] = (abs(res[f]["t_break"] - ref["t_break"]) / ref["t_break"]
+                                     if res[f]["t_break"] and ref["t_break"] else None)
+        res[f]["growth_rel_err"] = (abs(res[f]["growth_rate_x_tcap"] - ref["growth_rate_x_tcap"])
+                                    / ref["growth_rate_x_tcap"]
+                                    if res[f]["growth_rate_x_tcap"] and ref["growth_rate_x_tcap"] else None)
+    line = {
+        "metric": "storage precision vs FP64 (MRT Guo, G=-5.5, tau=1)",
+        "value": res["f32"]["err200_rho"], "unit": "max|rho - rho_FP64| after 200 steps (FP32)",
+        "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
+        "config": {"workload_200": f"ligament R0={args.R0:g} kR0={args.kR0:g} box {nx}x{ny}x{nz}",
+                   "workload_breakup": f"ligament R0={R0b:g} kR0={args.kR0:g} box {bx}x{by}x{bz}, "
+                                       f"diagnostics every {every} steps, t_cap={tcap:.1f}",
+                   "rho_ref": 1.0, "dev_scale": 1.0},
+        "formats": res,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.form == "batched":
         run_batched(args)
+    elif args.form == "adjoint":
+        run_adjoint(args)
+    elif args.form == "precision":
+        run_precision(args)
     else:
         run_ours(args)
 
