@@ -52,6 +52,9 @@ def parse_args():
     ap.add_argument("--storage", choices=list(BYTES_PER_POP), default="f32")
     ap.add_argument("--R0", type=float, default=64.0)
     ap.add_argument("--kR0", type=float, default=0.7)
+    ap.add_argument("--tau", type=float, default=1.0)
+    ap.add_argument("--mrt-rule", choices=["shear", "paper"], default="shear",
+                    help="MRT rates: shear moments at 1/tau (shear) or also the energy moment (paper)")
     ap.add_argument("--zchunk", type=int, default=0)
     ap.add_argument("--tile-y", type=int, default=0)
     ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 register-staged, 2 cp.async-staged")
@@ -62,6 +65,8 @@ def parse_args():
                     help="single: the sharp-interface ligament; batched: 64 uneven ligaments in one launch per "
                          "step; adjoint: gradients of the neck energy through 500 steps; precision: FP32/FP16/BF16 "
                          "storage against FP64")
+    ap.add_argument("--rho-ref", type=float, default=1.0,
+                    help="reference density of the 16-bit deviation formats")
     ap.add_argument("--breakup-R0", type=float, default=32.0,
                     help="precision form: ligament radius of the run-to-break-up comparison")
     return ap.parse_args()
@@ -72,9 +77,25 @@ def workload(args):
     nx, ny, nz = inputs.ligament_box(args.R0, args.kR0)
     forcing = "shift" if args.collision == "srt" else "guo"
     rl, rv = inputs.COEXISTENCE[(forcing, -5.5, 1.0)]
+    rule = f" ({args.mrt_rule} rule)" if args.collision == "mrt" else ""
     name = (f"ligament R0={args.R0:g} kR0={args.kR0:g} box {nx}x{ny}x{nz}, G=-5.5, "
-            f"{args.collision.upper()} tau=1, {args.storage.upper()} populations, 5% cosine perturbation")
+            f"{args.collision.upper()}{rule} tau={args.tau:g}, {args.storage.upper()} populations, "
+            f"5% cosine perturbation")
     return dict(nx=nx, ny=ny, nz=nz, rho_l=rl, rho_v=rv, name=name)
+
+
+def mrt_rates(args):
+    """Rates in moment order (rho e eps jx qx jy qy jz qz 3pxx 3pixx pww piww
+    pxy pyz pxz mx my mz): the five shear moments at 1/tau, plus the energy
+    moment for the paper's rule; the rest at 1.  None for SRT."""
+    if args.collision != "mrt":
+        return None
+    s = [1.0] * 19
+    for k in (9, 11, 13, 14, 15):
+        s[k] = 1.0 / args.tau
+    if args.mrt_rule == "paper":
+        s[1] = 1.0 / args.tau
+    return s
 
 
 def measured_hbm():
@@ -135,7 +156,7 @@ def oracle_mlups(w, args, slab, min_seconds, max_steps):
     from oracle import lbm_oracle as o
     from paper_1905_09554_gb300 import inputs
     rho = inputs.ligament_density(w["nx"], w["ny"], slab, args.R0, 0.05, w["rho_l"], w["rho_v"])
-    p = o.Params(G=-5.5, tau=1.0, collision=args.collision)
+    p = o.Params(G=-5.5, tau=args.tau, collision=args.collision, s=mrt_rates(args))
     f = o.init_populations(rho)
     f = o.step(f, p)  # warm-up
     t0, c0 = time.perf_counter(), os.times()
@@ -165,7 +186,7 @@ def run_reference(args):
     from oracle import lbm_oracle as o
     from paper_1905_09554_gb300 import inputs
     rho = inputs.ligament_density(w["nx"], w["ny"], slab, args.R0, 0.05, w["rho_l"], w["rho_v"])
-    p = o.Params(G=-5.5, tau=1.0, collision=args.collision)
+    p = o.Params(G=-5.5, tau=args.tau, collision=args.collision, s=mrt_rates(args))
     f = o.init_populations(rho)
     for _ in range(args.warmup):
         f = o.step(f, p)
@@ -233,8 +254,8 @@ def run_ours(args):
     w = workload(args)
     nx, ny, nz = w["nx"], w["ny"], w["nz"]
     ncell = nx * ny * nz
-    L = lbm.Lattice(nx, ny, nz, G=-5.5, tau=1.0, collision=args.collision, storage=args.storage,
-                    zchunk=args.zchunk, tile_y=args.tile_y, kernel=args.kernel)
+    L = lbm.Lattice(nx, ny, nz, G=-5.5, tau=args.tau, collision=args.collision, storage=args.storage,
+                    rates=mrt_rates(args), zchunk=args.zchunk, tile_y=args.tile_y, kernel=args.kernel)
     L.init_ligament(args.R0, 0.05, w["rho_l"], w["rho_v"])
     L_info = L.kernel_config()
     stream = torch.cuda.current_stream()
@@ -492,7 +513,8 @@ def run_precision(args):
     nx, ny, nz = inputs.ligament_box(args.R0, args.kR0)
     fields = {}
     for f in fmts:
-        with lbm.Lattice(nx, ny, nz, G=-5.5, tau=1.0, collision="mrt", rates=rates, storage=f) as L:
+        with lbm.Lattice(nx, ny, nz, G=-5.5, tau=1.0, collision="mrt", rates=rates, storage=f,
+                         rho_ref=args.rho_ref) as L:
             L.init_ligament(args.R0, 0.05, rl, rv)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -509,7 +531,8 @@ def run_precision(args):
     tcap = math.sqrt(rl * R0b ** 3 / sig) if sig else 1000.0
     every = 20
     for f in fmts:
-        with lbm.Lattice(bx, by, bz, G=-5.5, tau=1.0, collision="mrt", rates=rates, storage=f) as L:
+        with lbm.Lattice(bx, by, bz, G=-5.5, tau=1.0, collision="mrt", rates=rates, storage=f,
+                         rho_ref=args.rho_ref) as L:
             L.init_ligament(R0b, 0.05, rl, rv)
             ts, amps, mins = [], [], []
             t = 0
@@ -541,7 +564,7 @@ def run_precision(args):
         "config": {"workload_200": f"ligament R0={args.R0:g} kR0={args.kR0:g} box {nx}x{ny}x{nz}",
                    "workload_breakup": f"ligament R0={R0b:g} kR0={args.kR0:g} box {bx}x{by}x{bz}, "
                                        f"diagnostics every {every} steps, t_cap={tcap:.1f}",
-                   "rho_ref": 1.0, "dev_scale": 1.0},
+                   "rho_ref": args.rho_ref, "dev_scale": 1.0},
         "formats": res,
     }
     print(json.dumps(line), flush=True)

@@ -41,6 +41,7 @@ struct lbm_ctx {
     StepArgs args{};
     int zchunk = 0, tile_y = 8;
     int kernel = 1;                   // 1 register-staged, 2 cp.async, 3 pipelined
+    int coll = COLL_SRT;              // collision kernel (COLL_*)
     int grid = 0;                     // persistent grid size (kernels 2, 3)
     bool idx32 = false;               // 19 * cells fits 32-bit element offsets
     char err[512] = {0};
@@ -261,28 +262,34 @@ StepLaunch step_launch(const lbm_ctx* c) {
     l.tile_y = c->tile_y;
     l.grid = c->grid;
     l.idx32 = c->idx32;
-    l.coll = c->p.collision == LBM_MRT_GUO ? COLL_MRT : COLL_SRT;
+    l.coll = c->coll;
     l.stream = c->stream;
     return l;
 }
 
 int prepare_async(lbm_ctx* c) {
-    const StepLaunch l = step_launch(c);
-    switch (c->p.storage) {
-        case LBM_F64: return prepare_step_f64(l);
-        case LBM_F32: return prepare_step_f32(l);
-        default: return 0;
-    }
+    if (c->p.storage != LBM_F64 && c->p.storage != LBM_F32) return 0;
+    return step_kernels(c->p.storage, c->coll).prepare(step_launch(c));
 }
 
 cudaError_t launch_step(const lbm_ctx* c, const void* src, void* dst) {
-    const StepLaunch l = step_launch(c);
-    switch (c->p.storage) {
-        case LBM_F64: return launch_step_f64(l, src, dst);
-        case LBM_F16_DEV: return launch_step_f16(l, src, dst);
-        case LBM_BF16_DEV: return launch_step_bf16(l, src, dst);
-        default: return launch_step_f32(l, src, dst);
+    return step_kernels(c->p.storage, c->coll).launch(step_launch(c), src, dst);
+}
+
+// Collision kernel for the operator and rates: the MRT specialisations are
+// exact for rates equal to 1 outside the listed moments.
+int collision_kernel(const lbm_params& p, const double (&s)[Q]) {
+    if (p.collision != LBM_MRT_GUO) return COLL_SRT;
+    bool unit = true, sparse = true;
+    for (int k = 0; k < Q; ++k) {
+        if (k == 0 || k == 3 || k == 5 || k == 7) continue;  // conserved: rate irrelevant
+        const bool in_k = (k == 1 || k == 9 || k == 11 || k == 13 || k == 14 || k == 15);
+        if (s[k] != 1.0) {
+            unit = false;
+            if (!in_k) sparse = false;
+        }
     }
+    return unit ? COLL_MRT_UNIT : (sparse ? COLL_MRT_SPARSE : COLL_MRT);
 }
 
 // Run `fn.template operator()<Codec>()` for the context's storage type.
@@ -459,6 +466,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
             for (int k : rel) a.s[k] = 1.0 / p->tau;
         }
     }
+    c->coll = collision_kernel(*p, a.s);
     a.dev.rho_ref = float(p->rho_ref);
     a.dev.scale = float(p->dev_scale);
     a.dev.inv_scale = float(1.0 / p->dev_scale);
@@ -808,15 +816,14 @@ StepLaunch batch_launch(const lbm_batch* b) {
     l.tile_y = b->tile_y;
     l.grid = b->grid;
     l.idx32 = true;
-    l.coll = b->p.collision == LBM_MRT_GUO ? COLL_MRT : COLL_SRT;
+    l.coll = b->box[0]->coll;
     l.stream = b->stream;
     return l;
 }
 
 cudaError_t batch_launch_step(const lbm_batch* b, int from) {
     const StepLaunch l = batch_launch(b);
-    if (b->p.storage == LBM_F64) return launch_batch_step_f64(l, b->bargs, b->f[from], b->f[from ^ 1]);
-    return launch_batch_step_f32(l, b->bargs, b->f[from], b->f[from ^ 1]);
+    return step_kernels(b->p.storage, l.coll).batch(l, b->bargs, b->f[from], b->f[from ^ 1]);
 }
 
 void batch_drop_graphs(lbm_batch* b) {
@@ -834,7 +841,7 @@ lbm_status batch_configure(lbm_batch* b, int ty, int zc) {
         l.tile_y = ty;
         return l;
     }();
-    const int per_sm = b->p.storage == LBM_F64 ? prepare_batch_step_f64(probe) : prepare_batch_step_f32(probe);
+    const int per_sm = step_kernels(b->p.storage, probe.coll).batch_prepare(probe);
     if (per_sm < 1) return b->fail(LBM_ECUDA, "batch kernel cannot be resident (tile_y %d)", ty);
     std::vector<BatchBox> boxes(b->count);
     int items = 0;

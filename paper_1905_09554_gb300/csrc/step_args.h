@@ -9,7 +9,9 @@
 
 namespace lbm {
 
-enum { COLL_SRT = 0, COLL_MRT = 1 };
+// Collision kernels: SRT; MRT with general rates; MRT whose rates outside
+// {e, 3pxx, pww, pxy, pyz, pxz} are 1; MRT with every rate 1.
+enum { COLL_SRT = 0, COLL_MRT = 1, COLL_MRT_SPARSE = 2, COLL_MRT_UNIT = 3, COLL_COUNT = 4 };
 
 struct StepArgs {
     int nx, ny, nz;
@@ -47,26 +49,23 @@ struct StepLaunch {
     int tile_y;           // 4, 8 or 16 (tile width is 32)
     int grid;             // persistent grid (kernels 2 and 3)
     bool idx32;           // 32-bit element offsets (pipelined kernel)
-    int coll;             // COLL_SRT or COLL_MRT
+    int coll;             // COLL_SRT .. COLL_MRT_UNIT
     cudaStream_t stream;
 };
 
-// Per storage type (defined in step_<type>.cu).  launch_step_* enqueues one
-// step src -> dst; prepare_step_* opts kernels 2/3 in to their shared memory
-// and returns their resident blocks per SM (0 = the variant cannot run).
-cudaError_t launch_step_f64(const StepLaunch& l, const void* src, void* dst);
-cudaError_t launch_step_f32(const StepLaunch& l, const void* src, void* dst);
-cudaError_t launch_step_f16(const StepLaunch& l, const void* src, void* dst);
-cudaError_t launch_step_bf16(const StepLaunch& l, const void* src, void* dst);
-int prepare_step_f64(const StepLaunch& l);
-int prepare_step_f32(const StepLaunch& l);
-int prepare_step_f16(const StepLaunch& l);
-int prepare_step_bf16(const StepLaunch& l);
+// Kernel entry points of one (storage, collision) pair, defined in
+// step_<storage>_<collision>.cu.  launch enqueues one step src -> dst;
+// prepare opts kernels 2/3 in to their shared memory and returns their
+// resident blocks per SM (0 = cannot run); batch / batch_prepare do the same
+// for the batched step (FP64/FP32 only).
+struct StepKernels {
+    cudaError_t (*launch)(const StepLaunch& l, const void* src, void* dst);
+    int (*prepare)(const StepLaunch& l);
+    cudaError_t (*batch)(const StepLaunch& l, const BatchArgs& b, const void* src, void* dst);
+    int (*batch_prepare)(const StepLaunch& l);
+};
 
-// Batched step (pipelined kernel over many boxes; FP32 and FP64 storage).
-cudaError_t launch_batch_step_f64(const StepLaunch& l, const BatchArgs& b, const void* src, void* dst);
-cudaError_t launch_batch_step_f32(const StepLaunch& l, const BatchArgs& b, const void* src, void* dst);
-int prepare_batch_step_f64(const StepLaunch& l);
-int prepare_batch_step_f32(const StepLaunch& l);
+// storage: LBM_F64 .. LBM_BF16_DEV (0..3); coll: COLL_SRT .. COLL_MRT_UNIT.
+const StepKernels& step_kernels(int storage, int coll);
 
 }  // namespace lbm

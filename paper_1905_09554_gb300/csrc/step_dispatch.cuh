@@ -1,5 +1,6 @@
-// Template dispatch from a StepLaunch to the step kernel instantiations of one
-// storage codec; included by the per-storage translation units only.
+// Template dispatch from a StepLaunch to the step kernel instantiations of
+// one (storage codec, collision) pair.  Each step_<storage>_<collision>.cu
+// instantiates one pair, so the build compiles them in parallel.
 #pragma once
 #include "step_args.h"
 #include "step_kernel.cuh"
@@ -35,9 +36,6 @@ cudaError_t launch_step_t(const StepLaunch& c, const void* src, void* dst) {
     return cudaGetLastError();
 }
 
-// Prepare the cp.async kernel: opt in to its shared memory and size the
-// persistent grid from the occupancy calculator.  Returns 0 if the variant
-// cannot run for this storage/tile.
 template <class Codec, int COLL, int TY>
 int prepare_async_t(const StepLaunch& c) {
     constexpr int TX = 32;
@@ -69,36 +67,6 @@ int prepare_async_t(const StepLaunch& c) {
     return 0;
 }
 
-template <class Codec, int COLL>
-int prepare_async_c(const StepLaunch& c) {
-    switch (c.tile_y) {
-        case 4: return prepare_async_t<Codec, COLL, 4>(c);
-        case 16: return prepare_async_t<Codec, COLL, 16>(c);
-        default: return prepare_async_t<Codec, COLL, 8>(c);
-    }
-}
-
-template <class Codec, int COLL>
-cudaError_t launch_step_c(const StepLaunch& c, const void* src, void* dst) {
-    switch (c.tile_y) {
-        case 4: return launch_step_t<Codec, COLL, 4>(c, src, dst);
-        case 16: return launch_step_t<Codec, COLL, 16>(c, src, dst);
-        default: return launch_step_t<Codec, COLL, 8>(c, src, dst);
-    }
-}
-
-template <class Codec>
-cudaError_t launch_step_s(const StepLaunch& c, const void* src, void* dst) {
-    return c.coll == COLL_MRT ? launch_step_c<Codec, COLL_MRT>(c, src, dst)
-                                         : launch_step_c<Codec, COLL_SRT>(c, src, dst);
-}
-
-template <class Codec>
-int prepare_async_s(const StepLaunch& c) {
-    return c.coll == COLL_MRT ? prepare_async_c<Codec, COLL_MRT>(c) : prepare_async_c<Codec, COLL_SRT>(c);
-}
-
-// Batched pipelined step: one launch advances every box of the batch.
 template <class Codec, int COLL, int TY>
 cudaError_t launch_batch_t(const StepLaunch& c, const BatchArgs& b, const void* src, void* dst) {
     constexpr int TX = 32;
@@ -120,24 +88,59 @@ int prepare_batch_t(const StepLaunch&) {
     return per_sm;
 }
 
-template <class Codec>
-cudaError_t launch_batch_s(const StepLaunch& c, const BatchArgs& b, const void* src, void* dst) {
-    const bool mrt = c.coll == COLL_MRT;
+template <class Codec, int COLL>
+cudaError_t launch_step_cc(const StepLaunch& c, const void* src, void* dst) {
     switch (c.tile_y) {
-        case 4: return mrt ? launch_batch_t<Codec, COLL_MRT, 4>(c, b, src, dst) : launch_batch_t<Codec, COLL_SRT, 4>(c, b, src, dst);
-        case 16: return mrt ? launch_batch_t<Codec, COLL_MRT, 16>(c, b, src, dst) : launch_batch_t<Codec, COLL_SRT, 16>(c, b, src, dst);
-        default: return mrt ? launch_batch_t<Codec, COLL_MRT, 8>(c, b, src, dst) : launch_batch_t<Codec, COLL_SRT, 8>(c, b, src, dst);
+        case 4: return launch_step_t<Codec, COLL, 4>(c, src, dst);
+        case 16: return launch_step_t<Codec, COLL, 16>(c, src, dst);
+        default: return launch_step_t<Codec, COLL, 8>(c, src, dst);
     }
 }
 
-template <class Codec>
-int prepare_batch_s(const StepLaunch& c) {
-    const bool mrt = c.coll == COLL_MRT;
+template <class Codec, int COLL>
+int prepare_step_cc(const StepLaunch& c) {
     switch (c.tile_y) {
-        case 4: return mrt ? prepare_batch_t<Codec, COLL_MRT, 4>(c) : prepare_batch_t<Codec, COLL_SRT, 4>(c);
-        case 16: return mrt ? prepare_batch_t<Codec, COLL_MRT, 16>(c) : prepare_batch_t<Codec, COLL_SRT, 16>(c);
-        default: return mrt ? prepare_batch_t<Codec, COLL_MRT, 8>(c) : prepare_batch_t<Codec, COLL_SRT, 8>(c);
+        case 4: return prepare_async_t<Codec, COLL, 4>(c);
+        case 16: return prepare_async_t<Codec, COLL, 16>(c);
+        default: return prepare_async_t<Codec, COLL, 8>(c);
+    }
+}
+
+template <class Codec, int COLL>
+cudaError_t launch_batch_cc(const StepLaunch& c, const BatchArgs& b, const void* src, void* dst) {
+    switch (c.tile_y) {
+        case 4: return launch_batch_t<Codec, COLL, 4>(c, b, src, dst);
+        case 16: return launch_batch_t<Codec, COLL, 16>(c, b, src, dst);
+        default: return launch_batch_t<Codec, COLL, 8>(c, b, src, dst);
+    }
+}
+
+template <class Codec, int COLL>
+int prepare_batch_cc(const StepLaunch& c) {
+    switch (c.tile_y) {
+        case 4: return prepare_batch_t<Codec, COLL, 4>(c);
+        case 16: return prepare_batch_t<Codec, COLL, 16>(c);
+        default: return prepare_batch_t<Codec, COLL, 8>(c);
     }
 }
 
 }  // namespace lbm
+
+// Defines the kernel table entry of one (storage, collision) pair.
+#define LBM_STEP_INSTANCE(NAME, CODEC, COLL, WITH_BATCH)                                                \
+    namespace lbm {                                                                                   \
+    static cudaError_t launch_##NAME(const StepLaunch& l, const void* s, void* d) {                    \
+        return launch_step_cc<CODEC, COLL>(l, s, d);                                                  \
+    }                                                                                                 \
+    static int prepare_##NAME(const StepLaunch& l) { return prepare_step_cc<CODEC, COLL>(l); }         \
+    static cudaError_t batch_##NAME(const StepLaunch& l, const BatchArgs& b, const void* s, void* d) { \
+        if constexpr (WITH_BATCH) return launch_batch_cc<CODEC, COLL>(l, b, s, d);                    \
+        else return cudaErrorNotSupported;                                                            \
+    }                                                                                                 \
+    static int batch_prepare_##NAME(const StepLaunch& l) {                                            \
+        if constexpr (WITH_BATCH) return prepare_batch_cc<CODEC, COLL>(l);                            \
+        else return 0;                                                                                \
+    }                                                                                                 \
+    extern const StepKernels kStep_##NAME = {launch_##NAME, prepare_##NAME, batch_##NAME,             \
+                                             batch_prepare_##NAME};                                   \
+    }

@@ -190,6 +190,93 @@ __device__ __forceinline__ void collide_mrt(R (&f)[Q], R Fx, R Fy, R Fz, const d
     });
 }
 
+// MRT with Guo-like forcing when every rate outside K = {e, 3pxx, pww, pxy,
+// pyz, pxz} equals 1 (the paper's rule, and the shear rule), or when every
+// rate equals 1 (UNIT).  Writing m* = m_eq + S/2 + (1 - s)(m - m_eq + S/2),
+// the conserved rows vanish (rho: m = m_eq, S = 0; j: m - m_eq = -F/2,
+// S = F), rows with s = 1 vanish, and
+//   f* = f_eq(rho, u_b) + S_pop/2 + sum_{k in K} M_k^T (1 - s_k)(m_k - m_eq_k + S_k/2)/norm_k.
+// Algebraically identical to collide_mrt for such rates, with far fewer
+// operations (only the even rows of K are transformed).
+template <class R, bool UNIT>
+__device__ __forceinline__ void collide_mrt_sparse(R (&f)[Q], R Fx, R Fy, R Fz, const double (&s)[Q]) {
+    R ps[9], rho = f[0], jx = R(0), jy = R(0), jz = R(0);
+    static_for<0, 9>([&](auto pc) {
+        constexpr int p = decltype(pc)::value, q = 2 * p + 1;
+        ps[p] = f[q] + f[q + 1];
+        const R dif = f[q] - f[q + 1];
+        rho += ps[p];
+        if constexpr (cx(q) != 0) jx += R(cx(q)) * dif;
+        if constexpr (cy(q) != 0) jy += R(cy(q)) * dif;
+        if constexpr (cz(q) != 0) jz += R(cz(q)) * dif;
+    });
+    const R inv_rho = R(1) / rho;
+    const R ux = (jx + R(0.5) * Fx) * inv_rho;
+    const R uy = (jy + R(0.5) * Fy) * inv_rho;
+    const R uz = (jz + R(0.5) * Fz) * inv_rho;
+    const R ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+    const R u2 = ux2 + uy2 + uz2;
+    const R uF = ux * Fx + uy * Fy + uz * Fz;
+
+    // correction per even row of K, already divided by the row norm
+    constexpr int KS[6] = {1, 9, 11, 13, 14, 15};
+    R dk[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+    if constexpr (!UNIT) {
+        const R pxx = R(2) * ux2 - uy2 - uz2, pww = uy2 - uz2;
+        const R gxx = R(2) * ux * Fx - uy * Fy - uz * Fz, gww = uy * Fy - uz * Fz;
+        const R meq[6] = {rho * (R(-11) + R(19) * u2), rho * pxx, rho * pww, rho * ux * uy, rho * uy * uz,
+                          rho * ux * uz};
+        const R sg[6] = {R(38) * uF, R(2) * gxx, R(2) * gww, ux * Fy + uy * Fx, uy * Fz + uz * Fy, ux * Fz + uz * Fx};
+        static_for<0, 6>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr int k = KS[i];
+            R m = R(0);
+            constexpr int c0 = mrt_coef(k, 0);
+            if constexpr (c0 != 0) m = R(c0) * f[0];
+            static_for<0, 9>([&](auto pc) {
+                constexpr int p = decltype(pc)::value;
+                constexpr int c = mrt_coef(k, 2 * p + 1);
+                if constexpr (c == 1) m += ps[p];
+                else if constexpr (c == -1) m -= ps[p];
+                else if constexpr (c != 0) m += R(c) * ps[p];
+            });
+            dk[i] = (R(1) - R(s[k])) * (m - meq[i] + R(0.5) * sg[i]) * R(1.0 / mrt_norm(k));
+        });
+    }
+    auto corr = [&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        R acc = R(0);
+        if constexpr (!UNIT) {
+            static_for<0, 6>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                constexpr int c = mrt_coef(KS[i], q);
+                if constexpr (c == 1) acc += dk[i];
+                else if constexpr (c == -1) acc -= dk[i];
+                else if constexpr (c != 0) acc += R(c) * dk[i];
+            });
+        }
+        return acc;
+    };
+    const R base = R(1) - R(1.5) * u2;
+    f[0] = R(wq(0)) * (rho * base - R(1.5) * uF) + corr(std::integral_constant<int, 0>{});
+    static_for<0, 9>([&](auto pc) {
+        constexpr int q = 2 * decltype(pc)::value + 1;
+        R cu = R(0), cF = R(0);
+        if constexpr (cx(q) != 0) { cu += R(cx(q)) * ux; cF += R(cx(q)) * Fx; }
+        if constexpr (cy(q) != 0) { cu += R(cy(q)) * uy; cF += R(cy(q)) * Fy; }
+        if constexpr (cz(q) != 0) { cu += R(cz(q)) * uz; cF += R(cz(q)) * Fz; }
+        const R w = R(wq(q));
+        // f_eq = A +/- B; Guo source S/2 = E +/- O
+        const R A = w * rho * (base + R(4.5) * cu * cu);
+        const R B = w * rho * (R(3) * cu);
+        const R E = w * (R(-1.5) * uF + R(4.5) * cu * cF);
+        const R O = w * (R(1.5) * cF);
+        const R c = corr(std::integral_constant<int, q>{});  // even rows: equal on both members
+        f[q] = A + B + E + O + c;
+        f[q + 1] = A - B + E - O + c;
+    });
+}
+
 template <class Codec>
 __device__ __forceinline__ typename Codec::R cell_density(const typename Codec::S* __restrict__ p,
                                                           long long n, const DevParams& dev) {
@@ -225,7 +312,9 @@ __device__ __forceinline__ void update_cell(typename Codec::R (&fc)[Q], const ty
     const R Fx = gpsi * sx, Fy = gpsi * sy, Fz = gpsi * sz;
 
     if constexpr (COLL == COLL_SRT) collide_srt<R>(fc, Fx, Fy, Fz, R(a.tau), R(a.omega));
-    else collide_mrt<R>(fc, Fx, Fy, Fz, a.s);
+    else if constexpr (COLL == COLL_MRT) collide_mrt<R>(fc, Fx, Fy, Fz, a.s);
+    else if constexpr (COLL == COLL_MRT_SPARSE) collide_mrt_sparse<R, false>(fc, Fx, Fy, Fz, a.s);
+    else collide_mrt_sparse<R, true>(fc, Fx, Fy, Fz, a.s);
 
     // Eq. LBE streaming: f_a(x + c_a, t + 1) = f*_a(x, t).
     static_for<0, Q>([&](auto qc) {
@@ -561,8 +650,8 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src_all, typename Code
     const int n_items = BATCH ? b.n_items : a.n_items;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         int nx, ny, nz, tiles_x, n_tiles, zchunk, local;
-        const S* src;
-        S* dst;
+        const S* __restrict__ src;
+        S* __restrict__ dst;
         I n;
         if constexpr (BATCH) {
             int lo = 0, hi = b.nbox - 1;  // last box with item_begin <= item

@@ -99,6 +99,33 @@ def test_mrt_shear_rates_ragged_box(storage, tol):
         assert np.abs(u - u_ref).max() <= tol
 
 
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 2e-5)])
+def test_mrt_general_rates(storage, tol):
+    """Every non-conserved moment at its own rate in [0.7, 1.7]: the general
+    MRT kernel (the paper-rule and unit-rate kernels are exact
+    specialisations used when the rates allow)."""
+    s = 0.7 + np.random.default_rng(13).uniform(0.0, 1.0, 19)
+    rho = inputs.noisy_ligament_density(26, 19, 22, 5.0, 0.08, RLG, RVG, 1e-3, seed=12)
+    _, r_ref, u_ref, _ = oracle_run(rho, 30, tau=0.8, coll="mrt", s=s)
+    _, r, u = gpu_run(rho, 30, storage, coll="mrt", tau=0.8, rates=s)
+    assert np.abs(r - r_ref).max() <= tol
+    if storage == "f64":
+        assert np.abs(u - u_ref).max() <= tol
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 2e-5)])
+def test_mrt_unit_rates_at_tau_one(storage, tol):
+    """At tau = 1 with bulk and ghost rates 1 every rate is 1 (the shear-rule
+    benchmark case)."""
+    rho = inputs.noisy_ligament_density(30, 30, 40, 7.0, 0.05, RLG, RVG, 1e-3, seed=14)
+    s = o.mrt_rates(1.0, rule="shear")
+    _, r_ref, u_ref, _ = oracle_run(rho, 100, tau=1.0, coll="mrt", s=s)
+    _, r, u = gpu_run(rho, 100, storage, coll="mrt", tau=1.0, rates=s)
+    assert np.abs(r - r_ref).max() <= tol
+    if storage == "f64":
+        assert np.abs(u - u_ref).max() <= tol
+
+
 def test_fp64_mrt_paper_rates_at_tau_not_one():
     """Sec. 2 rate rule at tau = 0.7 (bulk and shear at 1/tau, ghosts 1), where
     MRT differs from BGK, G = -5.3."""
