@@ -43,7 +43,6 @@ struct lbm_ctx {
     int kernel = 1;                   // 1 register-staged, 2 cp.async, 3 pipelined
     int coll = COLL_SRT;              // collision kernel (COLL_*)
     int grid = 0;                     // persistent grid size (kernels 2, 3)
-    bool idx32 = false;               // 19 * cells fits 32-bit element offsets
     char err[512] = {0};
     lbm_batch* batch = nullptr;       // set when the context is a view of a batch box
     // discrete adjoint (allocated by lbm_adjoint_forward)
@@ -261,7 +260,6 @@ StepLaunch step_launch(const lbm_ctx* c) {
     l.kernel = c->kernel;
     l.tile_y = c->tile_y;
     l.grid = c->grid;
-    l.idx32 = c->idx32;
     l.coll = c->coll;
     l.stream = c->stream;
     return l;
@@ -408,7 +406,6 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     c->p = *p;
     c->stream = static_cast<cudaStream_t>(p->stream);
     c->n = n;
-    c->idx32 = (long long)Q * n < (1LL << 31);
     c->elem = p->storage == LBM_F64 ? 8 : (p->storage == LBM_F32 ? 4 : 2);
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -471,11 +468,13 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     a.dev.scale = float(p->dev_scale);
     a.dev.inv_scale = float(1.0 / p->dev_scale);
     // Auto launch shape (measured on GB300 at 256x256x575): FP32 runs the
-    // pipelined kernel, on 32x16 tiles for SRT and 32x4 tiles for MRT (whose
-    // collision needs more registers per cell); the other storage types run
-    // the register-staged kernel on 32x4 tiles.
+    // pipelined kernel, on 32x16 tiles for SRT and unit-rate MRT and on 32x4
+    // tiles for the other MRT kernels (their collision needs more registers
+    // per cell); the other storage types run the register-staged kernel on
+    // 32x4 tiles.
     const bool pipe_default = p->storage == LBM_F32;
-    const bool wide = p->collision == LBM_SRT_SHIFT && (p->kernel == 3 || (p->kernel == 0 && pipe_default));
+    const int coll = c->coll;
+    const bool wide = (coll == COLL_SRT || coll == COLL_MRT_UNIT) && (p->kernel == 3 || (p->kernel == 0 && pipe_default));
     c->tile_y = p->tile_y ? p->tile_y : (wide ? 16 : 4);
     if (p->kernel < 0 || p->kernel > 3) {
         snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel must be 0, 1, 2 or 3");
@@ -815,7 +814,6 @@ StepLaunch batch_launch(const lbm_batch* b) {
     l.kernel = 3;
     l.tile_y = b->tile_y;
     l.grid = b->grid;
-    l.idx32 = true;
     l.coll = b->box[0]->coll;
     l.stream = b->stream;
     return l;

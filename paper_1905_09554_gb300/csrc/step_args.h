@@ -48,7 +48,6 @@ struct StepLaunch {
     int kernel;           // 1 register-staged, 2 cp.async-staged, 3 pipelined
     int tile_y;           // 4, 8 or 16 (tile width is 32)
     int grid;             // persistent grid (kernels 2 and 3)
-    bool idx32;           // 32-bit element offsets (pipelined kernel)
     int coll;             // COLL_SRT .. COLL_MRT_UNIT
     cudaStream_t stream;
 };

@@ -14,12 +14,8 @@ cudaError_t launch_step_t(const StepLaunch& c, const void* src, void* dst) {
     if constexpr (sizeof(typename Codec::S) >= 4) {
         if (c.kernel == 3) {
             const size_t sm = PipeLayout<Codec, TX, TY>::bytes;
-            if (c.idx32)
-                sc_step_pipe_kernel<Codec, COLL, TX, TY, int><<<c.grid, TX * TY, sm, c.stream>>>(
-                    static_cast<const typename Codec::S*>(src), static_cast<typename Codec::S*>(dst), a, BatchArgs{});
-            else
-                sc_step_pipe_kernel<Codec, COLL, TX, TY, long long><<<c.grid, TX * TY, sm, c.stream>>>(
-                    static_cast<const typename Codec::S*>(src), static_cast<typename Codec::S*>(dst), a, BatchArgs{});
+            sc_step_pipe_kernel<Codec, COLL, TX, TY, long long><<<c.grid, TX * TY, sm, c.stream>>>(
+                static_cast<const typename Codec::S*>(src), static_cast<typename Codec::S*>(dst), a, BatchArgs{});
             return cudaGetLastError();
         }
     }
@@ -42,8 +38,7 @@ int prepare_async_t(const StepLaunch& c) {
     if constexpr (sizeof(typename Codec::S) >= 4) {
         if (c.kernel == 3) {
             using Lay = PipeLayout<Codec, TX, TY>;
-            auto kern = c.idx32 ? sc_step_pipe_kernel<Codec, COLL, TX, TY, int>
-                                 : sc_step_pipe_kernel<Codec, COLL, TX, TY, long long>;
+            auto kern = sc_step_pipe_kernel<Codec, COLL, TX, TY, long long>;
             if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes) !=
                 cudaSuccess)
                 return 0;
