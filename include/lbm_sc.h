@@ -80,7 +80,12 @@ typedef struct {
     int tile_y;           /* step kernel: tile height (4, 8 or 16); 0 = auto        */
     int kernel;           /* step kernel variant: 0 = auto, 1 = register-staged,
                              2 = cp.async-staged persistent, 3 = pipelined
-                             persistent (2 and 3: FP64/FP32 storage only)           */
+                             persistent (2 and 3: FP64/FP32 storage only),
+                             4 = warp-specialised bulk-copy (FP32, nx % 4 == 0)    */
+    int test_stall;       /* test only: with kernel 4 the copy warp issues nothing,
+                             so every bounded wait times out (about 1 s) and the
+                             next lbm_diag / lbm_moments / lbm_get_populations
+                             returns LBM_ETIMEOUT.  0 in normal use.               */
 } lbm_params;
 
 /* Fill *p with defaults: D3Q19, 32^3, G = -5.5, SRT tau = 1, psi exp, rho0 = 1,
@@ -156,7 +161,7 @@ lbm_status lbm_set_stream(lbm_ctx *ctx, void *stream);
 long long lbm_device_bytes(const lbm_ctx *ctx);
 
 /* Launch configuration the context chose for the step kernel: variant
- * (1 register-staged, 2 cp.async-staged, 3 pipelined), tile height, z planes
+ * (1 register-staged, 2 cp.async-staged, 3 pipelined, 4 bulk-copy), tile height, z planes
  * per work item and grid size (blocks).  Any pointer may be NULL. */
 lbm_status lbm_kernel_config(const lbm_ctx *ctx, int *kernel, int *tile_y,
                              int *zchunk, int *grid);

@@ -36,6 +36,7 @@ struct lbm_ctx {
     double* scratch = nullptr;        // staging / moments scratch (lazily grown)
     size_t scratch_bytes = 0;
     double* diag = nullptr;           // per-slice diagnostic partials (8 * nz)
+    int* dev_err = nullptr;           // device error word of the bounded waits
     std::vector<double> diag_host;
     long long own_bytes = 0;
     StepArgs args{};
@@ -316,6 +317,19 @@ lbm_status ensure_scratch(lbm_ctx* c, size_t bytes) {
     return LBM_OK;
 }
 
+// Read and clear the device error word: a bounded device wait that timed out
+// leaves the populations invalid.
+lbm_status check_device_error(lbm_ctx* c) {
+    int e = 0;
+    LBM_CUDA(c, cudaMemcpyAsync(&e, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (e) {
+        LBM_CUDA(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream));
+        return c->fail(LBM_ETIMEOUT, "a bounded device wait of the step kernel timed out; the populations are invalid");
+    }
+    return LBM_OK;
+}
+
 int auto_zchunk(const lbm_ctx* c) {
     const long long xy_blocks = (long long)((c->p.nx + 31) / 32) * ((c->p.ny + c->tile_y - 1) / c->tile_y);
     // Aim at ~4 blocks per SM in total so that the tail of the grid is short,
@@ -442,6 +456,17 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     }
     c->own_bytes += (long long)(sizeof(double) * 8 * (size_t)p->nz);
     c->diag_host.resize(8 * (size_t)p->nz);
+    e = cudaMalloc(&c->dev_err, 256);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->dev_err, 0, 256, c->stream);
+    if (e != cudaSuccess) {
+        snprintf(g_create_err, sizeof(g_create_err), "lbm_create: error-word allocation failed: %s",
+                 cudaGetErrorString(e));
+        cudaFree(c->diag);
+        if (c->own_f) { cudaFree(c->f[0]); cudaFree(c->f[1]); }
+        delete c;
+        return LBM_ENOMEM;
+    }
+    c->own_bytes += 256;
 
     // Kernel arguments.
     StepArgs& a = c->args;
@@ -464,6 +489,8 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
         }
     }
     c->coll = collision_kernel(*p, a.s);
+    a.err = c->dev_err;
+    a.test_stall = p->test_stall ? 1 : 0;
     a.dev.rho_ref = float(p->rho_ref);
     a.dev.scale = float(p->dev_scale);
     a.dev.inv_scale = float(1.0 / p->dev_scale);
@@ -476,8 +503,13 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     const int coll = c->coll;
     const bool wide = (coll == COLL_SRT || coll == COLL_MRT_UNIT) && (p->kernel == 3 || (p->kernel == 0 && pipe_default));
     c->tile_y = p->tile_y ? p->tile_y : (wide ? 16 : 4);
-    if (p->kernel < 0 || p->kernel > 3) {
-        snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel must be 0, 1, 2 or 3");
+    if (p->kernel == 4 && (p->storage != LBM_F32 || p->nx % 4 != 0)) {
+        snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel 4 needs FP32 storage and nx %% 4 == 0");
+        lbm_destroy(c);
+        return LBM_EINVAL;
+    }
+    if (p->kernel < 0 || p->kernel > 4) {
+        snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel must be 0, 1, 2, 3 or 4");
         lbm_destroy(c);
         return LBM_EINVAL;
     }
@@ -488,8 +520,14 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
         if (per_sm > 0) {
             c->grid = per_sm * c->num_sms;
         } else if (p->kernel >= 2) {
-            snprintf(g_create_err, sizeof(g_create_err),
-                     "lbm_create: kernel %d needs FP64/FP32 storage (kernel 2 with FP64: tile_y <= 8)", p->kernel);
+            if (per_sm < 0)
+                snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel %d cannot be configured: %s",
+                         p->kernel, cudaGetErrorString(cudaError_t(-per_sm)));
+            else
+                snprintf(g_create_err, sizeof(g_create_err),
+                         "lbm_create: kernel %d needs FP64/FP32 storage (kernel 2 with FP64: tile_y <= 8) "
+                         "and must fit on an SM",
+                         p->kernel);
             lbm_destroy(c);
             return LBM_EINVAL;
         } else {
@@ -534,6 +572,7 @@ void lbm_destroy(lbm_ctx* c) {
     }
     cudaFree(c->scratch);
     cudaFree(c->diag);
+    cudaFree(c->dev_err);
     cudaFree(c->adj.cp);
     cudaFree(c->adj.seg);
     cudaFree(c->adj.lam[0]);
@@ -651,6 +690,7 @@ lbm_status lbm_set_populations(lbm_ctx* c, const double* f, int on_device) {
 
 lbm_status lbm_get_populations(lbm_ctx* c, double* f, int on_device) {
     if (!c) return LBM_EINVAL;
+    if (lbm_status st = check_device_error(c); st != LBM_OK) return st;
     if (!f) return c->fail(LBM_EINVAL, "lbm_get_populations: f is NULL");
     if (on_device) {
         with_codec(c, [&](auto codec) {
@@ -696,6 +736,7 @@ lbm_status lbm_step(lbm_ctx* c, long nsteps) {
 
 lbm_status lbm_moments(lbm_ctx* c, double* rho, double* ux, double* uy, double* uz, int on_device) {
     if (!c) return LBM_EINVAL;
+    if (lbm_status st = check_device_error(c); st != LBM_OK) return st;
     const size_t nb = sizeof(double) * (size_t)c->n;
     double *d_rho, *d_ux, *d_uy, *d_uz;
     if (on_device) {
@@ -738,6 +779,7 @@ lbm_status lbm_moments(lbm_ctx* c, double* rho, double* ux, double* uy, double* 
 lbm_status lbm_diag(lbm_ctx* c, double rho_l, double rho_v, double* mass, double mom[3], double* area_z,
                     double* maxrho_z) {
     if (!c) return LBM_EINVAL;
+    if (lbm_status st = check_device_error(c); st != LBM_OK) return st;
     if (!(rho_l > rho_v)) return c->fail(LBM_EINVAL, "lbm_diag: need rho_l > rho_v");
     const auto& p = c->p;
     with_codec(c, [&](auto codec) {
@@ -840,7 +882,9 @@ lbm_status batch_configure(lbm_batch* b, int ty, int zc) {
         return l;
     }();
     const int per_sm = step_kernels(b->p.storage, probe.coll).batch_prepare(probe);
-    if (per_sm < 1) return b->fail(LBM_ECUDA, "batch kernel cannot be resident (tile_y %d)", ty);
+    if (per_sm < 1)
+        return b->fail(LBM_ECUDA, "batch kernel cannot be resident (tile_y %d): %s", ty,
+                       per_sm < 0 ? cudaGetErrorString(cudaError_t(-per_sm)) : "no block fits on an SM");
     std::vector<BatchBox> boxes(b->count);
     int items = 0;
     for (int i = 0; i < b->count; ++i) {

@@ -24,6 +24,8 @@ struct StepArgs {
     double rho0, inv_rho0;
     double s[Q];          // MRT rates, moment order
     DevParams dev;
+    int* err;             // device error word (bit 0: a bounded wait timed out)
+    int test_stall;       // failure test of the bounded waits (bulk kernel)
 };
 
 // One box of a batch: geometry, work items and where its populations start

@@ -11,6 +11,13 @@ template <class Codec, int COLL, int TY>
 cudaError_t launch_step_t(const StepLaunch& c, const void* src, void* dst) {
     constexpr int TX = 32;
     const StepArgs& a = c.args;
+    if constexpr (std::is_same_v<Codec, CodecF32>) {
+        if (c.kernel == 4) {
+            sc_step_bulk_kernel<COLL, TY><<<c.grid, BulkLayout<TY>::NT + 32, BulkLayout<TY>::bytes, c.stream>>>(
+                static_cast<const float*>(src), static_cast<float*>(dst), a);
+            return cudaGetLastError();
+        }
+    }
     if constexpr (sizeof(typename Codec::S) >= 4) {
         if (c.kernel == 3) {
             const size_t sm = PipeLayout<Codec, TX, TY>::bytes;
@@ -35,29 +42,34 @@ cudaError_t launch_step_t(const StepLaunch& c, const void* src, void* dst) {
 template <class Codec, int COLL, int TY>
 int prepare_async_t(const StepLaunch& c) {
     constexpr int TX = 32;
+    if constexpr (std::is_same_v<Codec, CodecF32>) {
+        if (c.kernel == 4) {
+            auto kern = sc_step_bulk_kernel<COLL, TY>;
+            const int sm = (int)BulkLayout<TY>::bytes;
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            int per_sm = 0;
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BulkLayout<TY>::NT + 32, sm);
+            return e == cudaSuccess ? per_sm : -int(e);
+        }
+    }
     if constexpr (sizeof(typename Codec::S) >= 4) {
         if (c.kernel == 3) {
             using Lay = PipeLayout<Codec, TX, TY>;
             auto kern = sc_step_pipe_kernel<Codec, COLL, TX, TY, long long>;
-            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes) !=
-                cudaSuccess)
-                return 0;
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes);
             int per_sm = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, Lay::bytes) != cudaSuccess)
-                return 0;
-            return per_sm;
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, Lay::bytes);
+            return e == cudaSuccess ? per_sm : -int(e);
         }
     }
     if constexpr (sizeof(typename Codec::S) >= 4 && (TY <= 8 || sizeof(typename Codec::S) == 4)) {
         using Lay = AsyncLayout<Codec, TX, TY>;
         auto kern = sc_step_async_kernel<Codec, COLL, TX, TY>;
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes) != cudaSuccess)
-            return 0;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes);
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, Lay::bytes) != cudaSuccess ||
-            per_sm < 1)
-            return 0;
-        return per_sm;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, Lay::bytes);
+        return e == cudaSuccess ? per_sm : -int(e);
     }
     return 0;
 }
@@ -76,11 +88,10 @@ int prepare_batch_t(const StepLaunch&) {
     constexpr int TX = 32;
     using Lay = PipeLayout<Codec, TX, TY>;
     auto kern = sc_step_pipe_kernel<Codec, COLL, TX, TY, int, true>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes) != cudaSuccess)
-        return 0;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, Lay::bytes) != cudaSuccess) return 0;
-    return per_sm;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, Lay::bytes);
+    return e == cudaSuccess ? per_sm : -int(e);
 }
 
 template <class Codec, int COLL>

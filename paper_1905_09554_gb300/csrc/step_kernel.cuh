@@ -779,4 +779,238 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src_all, typename Code
     async_copy::wait<0>();
 }
 
+// ----------------------------------------------------------------------------
+// Bulk-copy variant (FP32 storage, nx a multiple of 4).
+//
+// Warp-specialised: one producer warp fetches every plane of the tile plus a
+// 4-column / 1-row halo (x0-4 .. x0+35, y0-1 .. y0+TY) with cp.async.bulk
+// row copies (160 bytes each, split where the periodic wrap cuts a row) into
+// a three-stage shared-memory buffer, completing on an mbarrier per stage;
+// TX*TY consumer threads compute psi and collide from shared memory and
+// release a stage through a second mbarrier.  Periodic wrap is applied in the
+// copy addresses, so no fix-up is needed at box edges.  Every mbarrier wait is
+// bounded: on timeout the thread sets *a.err and stops waiting, so the kernel
+// always terminates (the host reports LBM_ETIMEOUT).
+// ----------------------------------------------------------------------------
+namespace bulk {
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void bar_init(unsigned long long* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void arrive(unsigned long long* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void arrive_expect_tx(unsigned long long* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool try_wait(unsigned long long* b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false (and *err set) if the phase did not complete within
+// about one second (2^31 SM clocks).  `bad` short-circuits every later wait
+// of the thread, so a stalled block finishes after one timeout per thread.
+__device__ __forceinline__ bool wait(unsigned long long* b, unsigned parity, bool& bad, int* err) {
+    if (bad) return false;
+    if (try_wait(b, parity)) return true;
+    const long long t0 = clock64();
+    while (clock64() - t0 < (1LL << 31))
+        if (try_wait(b, parity)) return true;
+    bad = true;
+    atomicOr(err, 1);
+    return false;
+}
+__device__ __forceinline__ void copy(void* dst, const void* src, unsigned bytes, unsigned long long* b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(b))
+                 : "memory");
+}
+}  // namespace bulk
+
+template <int TY>
+struct BulkLayout {
+    static constexpr int TX = 32;
+    static constexpr int NT = TX * TY;                  // consumer threads
+    static constexpr int NCW = NT / 32;                 // consumer warps
+    static constexpr int ROWS = TY + 2;
+    static constexpr int COLS = TX + 8;                 // x0-4 .. x0+TX+3
+    static constexpr int NSTAGE = 3;
+    static constexpr int PX = TX + 2;                   // psi ring pitch
+    static constexpr int PLANE = PX * (TY + 2);
+    static constexpr unsigned stage_floats = Q * ROWS * COLS;
+    static constexpr unsigned stage_bytes = stage_floats * 4;
+    static constexpr size_t bytes = NSTAGE * (size_t)stage_bytes + 4 * PLANE * 4 + 2 * NSTAGE * 8;
+};
+
+// Register budget: each of an SM's 4 sub-partitions holds 16384 registers
+// for the warps placed on it, so w resident warps allow 16384 / (32 ceil(w/4))
+// registers per thread: TY = 16, one block of 17 warps -> 96; TY = 8, two
+// blocks of 9 warps -> 96; TY = 4, three blocks of 5 warps -> 128.
+template <int COLL, int TY>
+__global__ void __maxnreg__(TY >= 8 ? 96 : 128)
+sc_step_bulk_kernel(const float* __restrict__ src, float* __restrict__ dst, const StepArgs a) {
+    using L = BulkLayout<TY>;
+    using R = float;
+    constexpr int TX = L::TX, NT = L::NT, ROWS = L::ROWS, COLS = L::COLS, PX = L::PX, PLANE = L::PLANE;
+    constexpr int NHALO = 2 * (TX + 2) + 2 * TY;
+    static_assert(NHALO <= NT, "tile too small for its halo ring");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float* stage = reinterpret_cast<float*>(smem_raw);
+    float* ring = stage + L::NSTAGE * L::stage_floats;
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(ring + 4 * PLANE);
+    unsigned long long* empty = full + L::NSTAGE;
+
+    const int tid = threadIdx.x;
+    const bool producer = tid >= NT;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const long long n = a.n;
+    const long long plane = (long long)nx * ny;
+    bool bad = false;
+
+    if (tid == 0) {
+        for (int s = 0; s < L::NSTAGE; ++s) {
+            bulk::bar_init(&full[s], 1);
+            bulk::bar_init(&empty[s], L::NCW);
+        }
+        bulk::fence_init();
+    }
+    __syncthreads();
+
+    unsigned g = 0;  // planes fetched so far by this block (same count on both sides)
+    if (producer) {
+        const int lane = tid - NT;
+        for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+            const int tile = item % a.n_tiles, chunk = item / a.n_tiles;
+            const int x0 = (tile % a.tiles_x) * TX, y0 = (tile / a.tiles_x) * TY;
+            const int zs = chunk * a.zchunk, ze = min(zs + a.zchunk, nz);
+            const int xs = wrap_index(x0 - 4, nx);
+            for (int p = zs - 1; p <= ze; ++p, ++g) {
+                const int s = g % L::NSTAGE;
+                if (a.test_stall) continue;  // failure test: the consumers' waits must time out
+                if (g >= (unsigned)L::NSTAGE) bulk::wait(&empty[s], ((g / L::NSTAGE) - 1) & 1, bad, a.err);
+                if (lane == 0) bulk::arrive_expect_tx(&full[s], L::stage_bytes);
+                __syncwarp();
+                if (!bad) {
+                    const int zw = p < 0 ? p + nz : (p >= nz ? p - nz : p);
+                    float* st = stage + s * L::stage_floats;
+                    for (int u = lane; u < Q * ROWS; u += 32) {
+                        const int q = u / ROWS, r = u % ROWS;
+                        const int y = wrap_index(y0 - 1 + r, ny);
+                        const float* row = src + (long long)q * n + (long long)zw * plane + (long long)y * nx;
+                        float* d = st + (q * ROWS + r) * COLS;
+                        int x = xs, left = COLS;
+                        while (left > 0) {  // split where the periodic wrap cuts the row
+                            const int piece = min(left, nx - x);
+                            bulk::copy(d, row + x, piece * 4, &full[s]);
+                            d += piece;
+                            left -= piece;
+                            x = 0;
+                        }
+                    }
+                }
+            }
+        }
+        // drain: the last planes' copies complete before the block exits
+        if (!a.test_stall)
+            for (unsigned k = (g > (unsigned)L::NSTAGE ? g - L::NSTAGE : 0); k < g; ++k)
+            bulk::wait(&full[k % L::NSTAGE], (k / L::NSTAGE) & 1, bad, a.err);
+        return;
+    }
+
+    // consumers
+    const int lx = tid % TX, ly = tid / TX;
+    const int warp = tid / 32, lane = tid % 32;
+    const R rho0 = R(a.rho0), inv_rho0 = R(a.inv_rho0);
+    const int my_slot = (ly + 1) * PX + (lx + 1);
+    const int my_st = (ly + 1) * COLS + (lx + 4);
+    int h_slot = -1, h_st = 0;
+    if (tid < NHALO) {
+        int hx, hy;
+        if (tid < PX) { hx = tid - 1; hy = -1; }
+        else if (tid < 2 * PX) { hx = tid - PX - 1; hy = TY; }
+        else { const int k = tid - 2 * PX; hx = (k < TY) ? -1 : TX; hy = (k < TY) ? k : k - TY; }
+        h_slot = (hy + 1) * PX + (hx + 1);
+        h_st = (hy + 1) * COLS + (hx + 4);
+    }
+    auto consumers_sync = [] { asm volatile("bar.sync 1, %0;\n" ::"n"(NT) : "memory"); };
+    auto release = [&](unsigned gi) {
+        __syncwarp();
+        if (lane == 0) bulk::arrive(&empty[gi % L::NSTAGE]);
+        (void)warp;
+    };
+
+    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+        const int tile = item % a.n_tiles, chunk = item / a.n_tiles;
+        const int x0 = (tile % a.tiles_x) * TX, y0 = (tile / a.tiles_x) * TY;
+        const int zs = chunk * a.zchunk, ze = min(zs + a.zchunk, nz);
+        const int gx = wrap_index(x0 + lx, nx), gy = wrap_index(y0 + ly, ny);
+        const bool active = (x0 + lx < nx) && (y0 + ly < ny);
+        const int xp = (gx + 1 == nx) ? 0 : gx + 1, xm = (gx == 0) ? nx - 1 : gx - 1;
+        const int yp = (gy + 1 == ny) ? 0 : gy + 1, ym = (gy == 0) ? ny - 1 : gy - 1;
+        const long long yoff[3] = {(long long)ym * nx, (long long)gy * nx, (long long)yp * nx};
+        const int xidx[3] = {xm, gx, xp};
+        const unsigned g0 = g;
+        auto st_of = [&](unsigned gi) { return stage + (gi % L::NSTAGE) * L::stage_floats; };
+        auto slot_of = [&](int z) { return (z - zs + 1) & 3; };
+        auto psi_from = [&](unsigned gi, int z) {
+            const float* st = st_of(gi);
+            R r = R(0);
+            static_for<0, Q>([&](auto qc) {
+                constexpr int q = decltype(qc)::value;
+                r += st[q * ROWS * COLS + my_st];
+            });
+            ring[slot_of(z) * PLANE + my_slot] = psi_of<R>(r, rho0, inv_rho0);
+            if (h_slot >= 0) {
+                R rh = R(0);
+                static_for<0, Q>([&](auto qc) {
+                    constexpr int q = decltype(qc)::value;
+                    rh += st[q * ROWS * COLS + h_st];
+                });
+                ring[slot_of(z) * PLANE + h_slot] = psi_of<R>(rh, rho0, inv_rho0);
+            }
+        };
+        auto wait_plane = [&](unsigned gi) { bulk::wait(&full[gi % L::NSTAGE], (gi / L::NSTAGE) & 1, bad, a.err); };
+
+        consumers_sync();  // the previous item's readers of the psi ring are done
+        wait_plane(g0);
+        psi_from(g0, zs - 1);
+        release(g0);
+        wait_plane(g0 + 1);
+        psi_from(g0 + 1, zs);
+        for (int z = zs; z < ze; ++z) {
+            const unsigned gi = g0 + (z - zs) + 1;  // plane z
+            wait_plane(gi + 1);
+            psi_from(gi + 1, z + 1);
+            consumers_sync();
+            if (active) {
+                const float* st = st_of(gi);
+                R fc[Q];
+                static_for<0, Q>([&](auto qc) {
+                    constexpr int q = decltype(qc)::value;
+                    fc[q] = st[q * ROWS * COLS + my_st];
+                });
+                const int zm = (z == 0) ? nz - 1 : z - 1;
+                const int zn = (z + 1 == nz) ? 0 : z + 1;
+                const long long zoff[3] = {(long long)zm * plane, (long long)z * plane, (long long)zn * plane};
+                update_cell<CodecF32, COLL, PX>(fc, ring + slot_of(z - 1) * PLANE, ring + slot_of(z) * PLANE,
+                                                ring + slot_of(z + 1) * PLANE, my_slot, dst, n, zoff, yoff, xidx,
+                                                a);
+            }
+            release(gi);
+        }
+        release(g0 + (ze - zs) + 1);  // plane ze: psi only
+        g = g0 + (ze - zs) + 2;
+    }
+}
+
 }  // namespace lbm

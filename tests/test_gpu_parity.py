@@ -154,13 +154,15 @@ def test_one_step_populations_on_a_rough_field(coll):
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 @pytest.mark.parametrize("coll", ["srt", "mrt"])
 def test_kernel_variant_tiling_and_chunking_do_not_change_a_bit(coll, storage):
-    """Register-staged, cp.async-staged and pipelined kernels, every tile
-    height and z-chunk length give bit-identical states."""
+    """Register-staged, cp.async-staged, pipelined and bulk-copy kernels,
+    every tile height and z-chunk length give bit-identical states."""
     rho = inputs.noisy_ligament_density(40, 12, 23, 3.0, 0.1, RL, RV, 1e-3, seed=2)
     ref = None
-    for kernel in (1, 2, 3):
+    for kernel in (1, 2, 3, 4):
         for tile_y in (4, 8, 16):
             if kernel == 2 and storage == "f64" and tile_y == 16:
+                continue
+            if kernel == 4 and storage != "f32":
                 continue
             for zchunk in (1, 5, 23):
                 f, _, _ = gpu_run(rho, 10, storage, coll=coll, tau=0.8, tile_y=tile_y, zchunk=zchunk,
@@ -168,6 +170,39 @@ def test_kernel_variant_tiling_and_chunking_do_not_change_a_bit(coll, storage):
                 if ref is None:
                     ref = f
                 assert np.array_equal(f, ref), (kernel, tile_y, zchunk)
+
+
+def test_bulk_kernel_on_boxes_that_wrap_inside_a_row():
+    """nx = 12 < the 40-column copy window: every row copy wraps several
+    times; ny = 5 and nz = 3 are smaller than a tile."""
+    rho = inputs.random_density(12, 5, 3, seed=17, lo=0.3, hi=1.9)
+    f4, _, _ = gpu_run(rho, 6, "f32", tau=0.9, kernel=4, tile_y=4)
+    f1, _, _ = gpu_run(rho, 6, "f32", tau=0.9, kernel=1, tile_y=4)
+    assert np.array_equal(f4, f1)
+
+
+def test_bounded_waits_time_out_and_the_context_survives():
+    """Failure test (no GPU fault): with test_stall the copy warp issues
+    nothing, every consumer wait gives up after about a second, the kernel
+    returns, and the next host-synchronising call reports LBM_ETIMEOUT.  A new
+    context on the same device then works normally."""
+    rho = inputs.random_density(32, 16, 8, seed=3)
+    with lbm.Lattice(32, 16, 8, storage="f32", kernel=4, tile_y=16, test_stall=1) as L:
+        L.set_density(rho)
+        L.step(1)
+        with pytest.raises(lbm.LbmError, match="LBM_ETIMEOUT"):
+            L.diag(2.0, 0.1)
+        L.diag(2.0, 0.1, raise_nonfinite=False)  # the error word was cleared
+    f4, _, _ = gpu_run(rho, 3, "f32", kernel=4, tile_y=16)
+    f1, _, _ = gpu_run(rho, 3, "f32", kernel=1)
+    assert np.array_equal(f4, f1)
+
+
+def test_bulk_kernel_needs_fp32_and_nx_multiple_of_4():
+    with pytest.raises(lbm.LbmError, match="LBM_EINVAL"):
+        lbm.Lattice(10, 8, 8, storage="f32", kernel=4)
+    with pytest.raises(lbm.LbmError, match="LBM_EINVAL"):
+        lbm.Lattice(8, 8, 8, storage="f64", kernel=4)
 
 
 @pytest.mark.parametrize("kernel", [2, 3])
