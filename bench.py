@@ -61,10 +61,13 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", choices=["single", "batched", "adjoint", "precision"], default="single",
+    ap.add_argument("--form", choices=["single", "batched", "adjoint", "precision", "paper"], default="single",
                     help="single: the sharp-interface ligament; batched: 64 uneven ligaments in one launch per "
                          "step; adjoint: gradients of the neck energy through 500 steps; precision: FP32/FP16/BF16 "
                          "storage against FP64")
+    ap.add_argument("--radii", default="14,28,42",
+                    help="paper form: ligament radii of Tables 1-2 to run (14..98)")
+    ap.add_argument("--collisions", default="srt,mrt", help="paper form: srt, mrt or both")
     ap.add_argument("--rho-ref", type=float, default=1.0,
                     help="reference density of the 16-bit deviation formats")
     ap.add_argument("--breakup-R0", type=float, default=32.0,
@@ -397,6 +400,62 @@ def load_traffic(args, ncell, info):
     return per * ncell if per is not None else None
 
 
+def run_paper(args):
+    """The paper's break-up experiment (Sec. 3-4, Tables 1-2, Fig. 2b) at its
+    own parameters: G0 = -5.3, Oh = 0.1, tau / rho_l / rho_v / t_cap of Table 1
+    (SRT) or Table 2 (MRT, rates of Sec. 2), a box Ly x Ly x Lx with two
+    wavelengths of a 10% perturbation along the ligament (the paper's x axis
+    is this code's z axis), FP32 populations, tanh profile of width 2.  Runs
+    until the ligament breaks (min over slices of max rho below the mid
+    density) and reports T_break / t_cap beside Fig. 2b's value."""
+    import numpy as np
+    import torch
+
+    from paper_1905_09554_gb300 import diagnostics as dg
+    from paper_1905_09554_gb300 import lbm
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    gold = os.path.join(ROOT, "tests", "golden")
+    tables = {"srt": np.loadtxt(os.path.join(gold, "paper_table1_srt.txt")),
+              "mrt": np.loadtxt(os.path.join(gold, "paper_table2_mrt.txt"))}
+    fig = np.loadtxt(os.path.join(gold, "paper_fig2b_breakup.txt"))
+    radii = [int(r) for r in args.radii.split(",") if r]
+    cases = []
+    for coll in [c for c in args.collisions.split(",") if c]:
+        for R0 in radii:
+            row = [r for r in tables[coll] if int(r[0]) == R0][0]
+            _, Lx, Ly, tau, tcap, rl, rv, sigma = row
+            nx, ny, nz = int(Ly), int(Ly), int(Lx)
+            fig_t = [f[2] for f in fig if int(f[0]) == (0 if coll == "srt" else 1) and int(f[1]) == R0][0]
+            every = max(1, int(tcap / 40))
+            with lbm.Lattice(nx, ny, nz, G=-5.3, tau=tau, collision=coll, storage="f32") as L:
+                L.init_ligament(float(R0), 0.1, rl, rv, n_waves=2)
+                ts, mins = [], []
+                t = 0
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                while t <= 20 * tcap:
+                    d = L.diag(rl, rv, raise_nonfinite=False)
+                    ts.append(t)
+                    mins.append(float(d["maxrho_z"].min()))
+                    if mins[-1] < 0.5 * (rl + rv) or d["status"] != 0:
+                        break
+                    L.step(every)
+                    t += every
+                torch.cuda.synchronize()
+                wall = time.perf_counter() - t0
+                cfg = L.kernel_config()
+            tb = dg.breakup_time(ts, mins, rl, rv)
+            cases.append({"collision": coll, "R0": R0, "box": [nx, ny, nz], "tau": tau, "t_cap": tcap,
+                          "rho_l": rl, "rho_v": rv, "steps": t, "diag_every": every,
+                          "T_break_over_tcap": tb / tcap if tb is not None else None,
+                          "fig2b_T_break": fig_t,
+                          "rel_diff": (tb / tcap - fig_t) / fig_t if tb is not None else None,
+                          "wall_s": wall, "glups": nx * ny * nz * t / wall / 1e9, "kernel": cfg})
+            print(json.dumps(cases[-1]), flush=True)
+    print(json.dumps({"metric": "paper break-up experiment (Fig. 2b) at the paper's parameters",
+                      "unit": "T_break / t_cap", "data": "synthetic", "cases": cases}), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -407,6 +466,8 @@ def main():
         run_adjoint(args)
     elif args.form == "precision":
         run_precision(args)
+    elif args.form == "paper":
+        run_paper(args)
     else:
         run_ours(args)
 

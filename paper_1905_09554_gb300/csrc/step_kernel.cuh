@@ -640,11 +640,17 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src_all, typename Code
     const DevParams dev = a.dev;
     const int my_slot = (ly + 1) * PX + (lx + 1);
 
+    // Ring cells are spread over all warps in contiguous runs (warp w takes
+    // cells [w*HC, w*HC + HC)), so every warp carries the same extra work
+    // before the per-plane barrier.
+    constexpr int NW = TX * TY / 32, HC = (NH + NW - 1) / NW;
+    static_assert(HC <= 32, "ring run longer than a warp");
     int hx = 0, hy = 0, h_slot = -1;
-    if (tid < NH) {
-        if (tid < PX) { hx = tid - 1; hy = -1; }
-        else if (tid < 2 * PX) { hx = tid - PX - 1; hy = TY; }
-        else { const int k = tid - 2 * PX; hx = (k < TY) ? -1 : TX; hy = (k < TY) ? k : k - TY; }
+    const int h = (tid / 32) * HC + (tid % 32);
+    if ((tid % 32) < HC && h < NH) {
+        if (h < PX) { hx = h - 1; hy = -1; }
+        else if (h < 2 * PX) { hx = h - PX - 1; hy = TY; }
+        else { const int k = h - 2 * PX; hx = (k < TY) ? -1 : TX; hy = (k < TY) ? k : k - TY; }
         h_slot = (hy + 1) * PX + (hx + 1);
     }
 
@@ -700,7 +706,7 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src_all, typename Code
                 S* st = hstage + stage_of(z) * (Q * NH);
                 static_for<0, Q>([&](auto qc) {
                     constexpr int q = decltype(qc)::value;
-                    async_copy::copy<sizeof(S)>(st + q * NH + tid, base + I(q) * n);
+                    async_copy::copy<sizeof(S)>(st + q * NH + h, base + I(q) * n);
                 });
             }
             async_copy::commit();
@@ -711,7 +717,7 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src_all, typename Code
                 R r = R(0);
                 static_for<0, Q>([&](auto qc) {
                     constexpr int q = decltype(qc)::value;
-                    r += Codec::template decode<q>(st[q * NH + tid], dev);
+                    r += Codec::template decode<q>(st[q * NH + h], dev);
                 });
                 ring[slot_of(z) * PLANE + h_slot] = psi_of<R>(r, rho0, inv_rho0);
             }
