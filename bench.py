@@ -37,7 +37,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "D3Q19 SC-LBM MLUPS & % HBM peak; FP32/FP16 & batched vs FP64 at stated error"
-BYTES_PER_POP = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+BYTES_PER_POP = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "f16l": 2, "bf16l": 2}
+# local-reference formats also read and write a float reference density per cell
+EXTRA_BYTES_PER_CELL = {"f16l": 8, "bf16l": 8}
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_NAMES = {1: "sc_step_kernel", 2: "sc_step_async_kernel", 3: "sc_step_pipe_kernel"}
 
@@ -328,7 +330,7 @@ def run_ours(args):
         return
 
     peak, src = measured_hbm()
-    bpc = 2 * 19 * BYTES_PER_POP[args.storage]
+    bpc = 2 * 19 * BYTES_PER_POP[args.storage] + EXTRA_BYTES_PER_CELL.get(args.storage, 0)
     kname = KERNEL_NAMES.get(L_info["kernel"], "sc_step_kernel")
     rec = step_record()
     if args.storage == "f64" and rec and rec.get("fp64_flops_per_cell"):
@@ -398,6 +400,197 @@ def load_traffic(args, ncell, info):
     key = f"{args.collision}_{args.storage}_tau{args.tau:g}_k{info['kernel']}_ty{info['tile_y']}"
     per = rec.get("bytes_per_cell", {}).get(key)
     return per * ncell if per is not None else None
+
+
+def run_batched(args):
+    """64 independent ligaments (R0 in {8, 12, 16}, kR0 uniform on [0.2, 1.0)
+    from seed 0, box 4R0 x 4R0 x round(2 pi R0 / kR0)), FP32 SRT tau = 1,
+    G = -5.5, 3% perturbation, advanced together by one launch per step
+    (pairs of steps from a CUDA graph) after the launch-shape autotuner.
+    `value` is ligaments/s: complete runs of --steps steps per second."""
+    import torch
+
+    from paper_1905_09554_gb300 import inputs, lbm
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    insts = inputs.batch_instances(64, seed=0)
+    dims = [(d["nx"], d["ny"], d["nz"]) for d in insts]
+    rl, rv = inputs.COEXISTENCE[("shift", -5.5, 1.0)]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        B = lbm.Batch(dims, G=-5.5, tau=1.0, collision="srt", storage="f32", stream=stream.cuda_stream)
+        best = B.tune(trial_steps=3)
+        for box, d in zip(B.boxes, insts):
+            box.init_ligament(d["R0"], 0.03, rl, rv)
+        B.step(args.warmup)
+        cfg = B.config()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        B.step(args.steps)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        B.close()
+    cells = cfg["cells"]
+    line = {
+        "metric": "batched ligaments/s (64 uneven ligaments, one launch per step)",
+        "value": None,
+        "unit": "ligaments/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "64 ligaments, R0 in {8,12,16}, kR0 ~ U[0.2,1.0) seed 0, boxes 4R0x4R0xround(2piR0/kR0), "
+                               "G=-5.5, SRT tau=1, FP32, 3% perturbation",
+                   "cells": cells, "tile_y": cfg["tile_y"], "zchunk": cfg["zchunk"], "grid": cfg["grid"],
+                   "autotune_ms_per_step": best["ms_per_step"]},
+        "aggregate_mlups": cells * args.steps / (ms / 1e3) / 1e6,
+        "roofline": {"bound": "hbm", "achieved": 152 * cells / (ms / args.steps / 1e3) / 1e9,
+                     "peak": measured_hbm()[0], "unit": "GB/s"},
+        "gpu_launches": args.steps,
+    }
+    line["value"] = 64.0 / (ms / 1e3 * 3000.0 / args.steps)
+    line["roofline"]["frac"] = line["roofline"]["achieved"] / line["roofline"]["peak"]
+    print(json.dumps(line), flush=True)
+
+
+def golden_sigma(forcing):
+    path = os.path.join(ROOT, "tests", "golden", "sigma.json")
+    try:
+        with open(path) as fh:
+            return [c for c in json.load(fh)["cases"] if c["forcing"] == forcing][0]["sigma"]
+    except Exception:
+        return None
+
+
+def run_adjoint(args):
+    """Gradient of the neck energy J = mean_z (R(z) - mean R)^2 at step 500 with
+    respect to the initial density, G and tau, for the 64 x 64 x 180 ligament
+    (R0 = 16, kR0 = 0.56, 5% perturbation plus N(0, 1e-3) per-cell noise from
+    seed 1), SRT tau = 1, G = -5.5, FP32 populations, checkpoints every 23
+    steps.  `value` is adjoint steps/s of the backward pass (which includes
+    recomputing each segment from its checkpoint); the FP64 gradient of the
+    same problem is the accuracy reference."""
+    import numpy as np
+    import torch
+
+    from paper_1905_09554_gb300 import inputs, lbm
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    nx, ny, nz = 64, 64, 180
+    R0, T, every = 16.0, 500, 23
+    rl, rv = inputs.COEXISTENCE[("shift", -5.5, 1.0)]
+    rho0 = inputs.noisy_ligament_density(nx, ny, nz, R0, 0.05, rl, rv, 1e-3, seed=1)
+
+    def dJ(rho):
+        A = ((rho - rv) / (rl - rv)).sum(axis=(1, 2))
+        R = np.sqrt(A / np.pi)
+        g = (2.0 / nz) * (R - R.mean()) / (2.0 * np.pi * R * (rl - rv))
+        return np.broadcast_to(g[:, None, None], rho.shape).copy(), float(((R - R.mean()) ** 2).mean())
+
+    out = {}
+    for storage in ("f32", "f64"):
+        with lbm.Lattice(nx, ny, nz, G=-5.5, tau=1.0, storage=storage) as L:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            L.adjoint_forward(rho0, T, every)
+            r, _ = L.moments()
+            t1 = time.perf_counter()
+            g, J = dJ(r)
+            t2 = time.perf_counter()
+            grad, gG, gT = L.adjoint_backward(g)
+            t3 = time.perf_counter()
+        out[storage] = dict(J=J, grad=grad, dG=gG, dtau=gT, fwd_s=t1 - t0, bwd_s=t3 - t2)
+    a, b = out["f32"], out["f64"]
+    line = {
+        "metric": "adjoint steps/s (SRT, 64x64x180, 500 steps, checkpoints every 23)",
+        "value": T / a["bwd_s"], "unit": "adjoint steps/s", "n_gpus": 1, "steps": T, "warmup": 0,
+        "ms_per_step": a["bwd_s"] / T * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "ligament 64x64x180, R0=16, kR0=0.56, 5% perturbation + N(0,1e-3) noise seed 1, "
+                               "G=-5.5, SRT tau=1, objective: neck energy at step 500",
+                   "checkpoint_every": every, "cells": nx * ny * nz},
+        "forward_with_checkpoints_steps_per_s": T / a["fwd_s"],
+        "fp64": {"adjoint_steps_per_s": T / b["bwd_s"], "dJ_dG": b["dG"], "dJ_dtau": b["dtau"], "J": b["J"]},
+        "fp32": {"dJ_dG": a["dG"], "dJ_dtau": a["dtau"], "J": a["J"]},
+        "fp32_vs_fp64": {"dJ_dG_rel": abs(a["dG"] - b["dG"]) / abs(b["dG"]),
+                         "dJ_dtau_rel": abs(a["dtau"] - b["dtau"]) / abs(b["dtau"]),
+                         "dJ_drho0_maxabs_rel": float(np.abs(a["grad"] - b["grad"]).max() / np.abs(b["grad"]).max())},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_precision(args):
+    """Population storage formats against the FP64 run (MRT, G = -5.5,
+    tau = 1, shear rule): max-abs rho and u error after 200 steps of the
+    R0 = --R0 ligament (kR0 = 0.7, 5% perturbation), and the growth rate and
+    break-up time of the R0 = --breakup-R0 ligament run to break-up."""
+    import numpy as np
+    import torch
+
+    from paper_1905_09554_gb300 import diagnostics as dg
+    from paper_1905_09554_gb300 import inputs, lbm
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rl, rv = inputs.COEXISTENCE[("guo", -5.5, 1.0)]
+    rates = [1.0] * 19  # shear rule at tau = 1: every rate is 1
+    sig = golden_sigma("guo")
+    fmts = ["f64", "f32", "f16", "bf16", "f16l", "bf16l"]
+    res = {f: {} for f in fmts}
+    nx, ny, nz = inputs.ligament_box(args.R0, args.kR0)
+    fields = {}
+    for f in fmts:
+        with lbm.Lattice(nx, ny, nz, G=-5.5, tau=1.0, collision="mrt", rates=rates, storage=f,
+                         rho_ref=args.rho_ref) as L:
+            L.init_ligament(args.R0, 0.05, rl, rv)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            L.step(200)
+            torch.cuda.synchronize()
+            res[f]["mlups_200"] = nx * ny * nz * 200 / (time.perf_counter() - t0) / 1e6
+            fields[f] = L.moments()
+    for f in fmts[1:]:
+        res[f]["err200_rho"] = float(np.abs(fields[f][0] - fields["f64"][0]).max())
+        res[f]["err200_u"] = float(np.abs(fields[f][1] - fields["f64"][1]).max())
+    del fields
+    R0b = args.breakup_R0
+    bx, by, bz = inputs.ligament_box(R0b, args.kR0)
+    tcap = math.sqrt(rl * R0b ** 3 / sig) if sig else 1000.0
+    every = 20
+    for f in fmts:
+        with lbm.Lattice(bx, by, bz, G=-5.5, tau=1.0, collision="mrt", rates=rates, storage=f,
+                         rho_ref=args.rho_ref) as L:
+            L.init_ligament(R0b, 0.05, rl, rv)
+            ts, amps, mins = [], [], []
+            t = 0
+            while t <= 60 * tcap:
+                d = L.diag(rl, rv, raise_nonfinite=False)
+                ts.append(t)
+                amps.append(dg.mode_amplitude(d["area_z"]))
+                mins.append(float(d["maxrho_z"].min()))
+                if mins[-1] < 0.5 * (rl + rv) or d["status"] != 0:
+                    break
+                L.step(every)
+                t += every
+        tb = dg.breakup_time(ts, mins, rl, rv)
+        w = dg.growth_rate(ts, amps, t_start=tcap, a_stop=0.3 * R0b)
+        res[f]["t_break"] = tb
+        res[f]["t_break_over_tcap"] = tb / tcap if tb is not None else None
+        res[f]["growth_rate_x_tcap"] = w * tcap if w is not None else None
+    for f in fmts[1:]:
+        ref = res["f64"]
+        res[f]["t_break_rel_err"] = (abs(res[f]["t_break"] - ref["t_break"]) / ref["t_break"]
+                                     if res[f]["t_break"] and ref["t_break"] else None)
+        res[f]["growth_rel_err"] = (abs(res[f]["growth_rate_x_tcap"] - ref["growth_rate_x_tcap"])
+                                    / ref["growth_rate_x_tcap"]
+                                    if res[f]["growth_rate_x_tcap"] and ref["growth_rate_x_tcap"] else None)
+    line = {
+        "metric": "storage precision vs FP64 (MRT Guo, G=-5.5, tau=1)",
+        "value": res["f32"]["err200_rho"], "unit": "max|rho - rho_FP64| after 200 steps (FP32)",
+        "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
+        "config": {"workload_200": f"ligament R0={args.R0:g} kR0={args.kR0:g} box {nx}x{ny}x{nz}",
+                   "workload_breakup": f"ligament R0={R0b:g} kR0={args.kR0:g} box {bx}x{by}x{bz}, "
+                                       f"diagnostics every {every} steps, t_cap={tcap:.1f}",
+                   "rho_ref": args.rho_ref, "dev_scale": 1.0},
+        "formats": res,
+    }
+    print(json.dumps(line), flush=True)
 
 
 def run_paper(args):
