@@ -53,7 +53,11 @@ enum { LBM_PSI_EXP = 0 };                      /* psi = rho0 (1 - exp(-rho/rho0)
 enum { LBM_F64 = 0,                            /* populations stored as double      */
        LBM_F32 = 1,                            /* stored as float, float arithmetic */
        LBM_F16_DEV = 2,                        /* half  deviations, float arithmetic */
-       LBM_BF16_DEV = 3 };                     /* bf16 deviations, float arithmetic  */
+       LBM_BF16_DEV = 3,                       /* bf16 deviations, float arithmetic  */
+       LBM_F16_LOCAL = 4,                      /* half  deviations from a per-cell
+                                                  reference density, float arithmetic */
+       LBM_BF16_LOCAL = 5 };                   /* bf16 deviations from a per-cell
+                                                  reference density, float arithmetic */
 
 typedef struct {
     int lattice;          /* LBM_D3Q19                                              */
@@ -68,8 +72,19 @@ typedef struct {
                              pyz, pxz relax at 1/tau, the rest at 1.              */
     int psi;              /* LBM_PSI_EXP                                            */
     double rho0;          /* reference density of psi (the paper fixes 1.0)        */
-    int storage;          /* LBM_F64 / LBM_F32 / LBM_F16_DEV / LBM_BF16_DEV          */
-    double rho_ref;       /* deviation storage: f_a = w_a rho_ref + d_a / dev_scale */
+    int storage;          /* LBM_F64 / LBM_F32 / LBM_F16_DEV / LBM_BF16_DEV /
+                             LBM_F16_LOCAL / LBM_BF16_LOCAL                          */
+    double rho_ref;       /* deviation storage: f_a = w_a rho_ref + d_a / dev_scale.
+                             Local-reference storage ignores it: there rho_ref is
+                             a float field R(x) the library allocates (2 x 4 bytes
+                             per cell beside the populations), set from each cell's
+                             density whenever the populations are set or
+                             initialised, and by every step to the density of the
+                             cell before the step (so f(t+1) is stored relative to
+                             rho(t), which differs from rho(t+1) by O(|div j|)).
+                             Local-reference storage runs step kernel 1 only and is
+                             not accepted by batches, the adjoint or
+                             lbm_diag_noalloc.                                        */
     double dev_scale;     /* deviation storage scale (> 0)                          */
     void *stream;         /* cudaStream_t for all work; NULL = legacy default       */
     void *f_a, *f_b;      /* optional caller-owned device buffers for the two
@@ -81,7 +96,11 @@ typedef struct {
     int kernel;           /* step kernel variant: 0 = auto, 1 = register-staged,
                              2 = cp.async-staged persistent, 3 = pipelined
                              persistent (2 and 3: FP64/FP32 storage only),
-                             4 = warp-specialised bulk-copy (FP32, nx % 4 == 0)    */
+                             4 = warp-specialised bulk-copy (FP32, nx % 4 == 0),
+                             5 = tensor-copy pipeline (FP32, tile_y 8 or 16,
+                             nx % 32 == 0, ny % tile_y == 0; steps on buffers
+                             other than the two copies, e.g. the adjoint's
+                             recomputation, run kernel 3)                           */
     int test_stall;       /* test only: with kernel 4 the copy warp issues nothing,
                              so every bounded wait times out (about 1 s) and the
                              next lbm_diag / lbm_moments / lbm_get_populations
@@ -245,8 +264,10 @@ lbm_status lbm_batch_config(const lbm_batch *b, int *tile_y, int *zchunk,
  * in which cudaMalloc/cudaFree would implicitly synchronise the device.
  * lbm_create allocates; this call does not.  It needs no context: the caller
  * passes its own population array f (device memory, 19*nx*ny*nz elements of
- * `storage` in the library's velocity order and field layout; rho_ref and
- * dev_scale as in lbm_params for the deviation formats) and its own outputs,
+ * `storage` in the library's velocity order and field layout, LBM_F64 ..
+ * LBM_BF16_DEV; rho_ref and dev_scale as in lbm_params for the deviation
+ * formats; the local-reference formats also need a context's density field
+ * and get LBM_EINVAL) and its own outputs,
  * and gets the same quantities as lbm_diag (mass, mom[3], area_z[nz],
  * maxrho_z[nz]; area_z/maxrho_z may be NULL).  Outputs are host memory when
  * on_device is 0, device memory when it is 1.  Work runs on `stream`

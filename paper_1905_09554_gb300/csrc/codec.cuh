@@ -10,6 +10,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "lattice.cuh"
 
 namespace lbm {
@@ -21,6 +23,7 @@ struct DevParams {
 };
 
 struct CodecF64 {
+    static constexpr bool kLocal = false;
     using S = double;
     using R = double;
     static constexpr int kStorage = 0;
@@ -33,6 +36,7 @@ struct CodecF64 {
 };
 
 struct CodecF32 {
+    static constexpr bool kLocal = false;
     using S = float;
     using R = float;
     static constexpr int kStorage = 1;
@@ -45,6 +49,7 @@ struct CodecF32 {
 };
 
 struct CodecF16Dev {
+    static constexpr bool kLocal = false;
     using S = __half;
     using R = float;
     static constexpr int kStorage = 2;
@@ -61,6 +66,7 @@ struct CodecF16Dev {
 };
 
 struct CodecBF16Dev {
+    static constexpr bool kLocal = false;
     using S = __nv_bfloat16;
     using R = float;
     static constexpr int kStorage = 3;
@@ -75,6 +81,49 @@ struct CodecBF16Dev {
         *p = __float2bfloat16_rn((v - float(wq(q)) * d.rho_ref) * d.scale);
     }
 };
+
+
+// Local-reference 16-bit storage: each cell also keeps, in a float field,
+// the density it had at the previous step, and each stored population is the
+// deviation from the rest equilibrium at that density,
+// d_a = (f_a - w_a rho_ref(cell)) * scale.  The writer of a population knows
+// the destination cell's current density (it is in the block's density
+// planes), and the reader needs only its own cell's reference.
+template <class S16>
+struct CodecLocal16 {
+    static constexpr bool kLocal = true;
+    using S = S16;
+    using R = float;
+    static constexpr int kStorage = std::is_same<S16, __half>::value ? 4 : 5;
+    __device__ __forceinline__ static float to_f(S v) {
+        if constexpr (std::is_same<S16, __half>::value) return __half2float(v);
+        else return __bfloat162float(v);
+    }
+    __device__ __forceinline__ static S from_f(float v) {
+        if constexpr (std::is_same<S16, __half>::value) return __float2half_rn(v);
+        else return __float2bfloat16_rn(v);
+    }
+    template <int q>
+    __device__ __forceinline__ static R decode_ref(S v, float ref, const DevParams& d) {
+        return float(wq(q)) * ref + to_f(v) * d.inv_scale;
+    }
+    template <int q>
+    __device__ __forceinline__ static R load_ref(const S* p, float ref, const DevParams& d) {
+        return decode_ref<q>(__ldg(p), ref, d);
+    }
+    template <int q>
+    __device__ __forceinline__ static void store_ref(S* p, R v, float ref, const DevParams& d) {
+        *p = from_f((v - float(wq(q)) * ref) * d.scale);
+    }
+    __device__ __forceinline__ static double decode_rt(const S* p, float w, float ref, const DevParams& d) {
+        return double(w * ref + to_f(*p) * d.inv_scale);
+    }
+    __device__ __forceinline__ static void encode_rt(S* p, float w, double v, float ref, const DevParams& d) {
+        *p = from_f((float(v) - w * ref) * d.scale);
+    }
+};
+using CodecF16Local = CodecLocal16<__half>;
+using CodecBF16Local = CodecLocal16<__nv_bfloat16>;
 
 // Runtime (non-templated) decode/encode for the conversion kernels.
 template <class Codec>

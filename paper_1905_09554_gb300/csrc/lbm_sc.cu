@@ -1,6 +1,7 @@
 // C ABI of the D3Q19 Shan-Chen lattice Boltzmann library (include/lbm_sc.h):
 // context management, initial states, the time-step driver, moments and
 // diagnostics.  The fused step kernel lives in step_kernel.cuh.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -29,6 +30,7 @@ struct lbm_ctx {
     int num_sms = 0;
     void* f[2] = {nullptr, nullptr};  // population copies; f[cur] is the state
     bool own_f = false;
+    float* ref[2] = {nullptr, nullptr};  // local-reference storage: density field paired with f[k]
     int cur = 0;
     long t = 0;
     long long n = 0;
@@ -41,7 +43,9 @@ struct lbm_ctx {
     long long own_bytes = 0;
     StepArgs args{};
     int zchunk = 0, tile_y = 8;
-    int kernel = 1;                   // 1 register-staged, 2 cp.async, 3 pipelined
+    int kernel = 1;                   // 1 register-staged, 2 cp.async, 3 pipelined, 4 bulk, 5 tensor
+    CUtensorMap tmap[2];              // kernel 5: tensor maps of the two population copies
+    int grid3 = 0;                    // kernel 5: grid of the pipelined kernel used for other buffers
     int coll = COLL_SRT;              // collision kernel (COLL_*)
     int grid = 0;                     // persistent grid size (kernels 2, 3)
     char err[512] = {0};
@@ -100,21 +104,36 @@ __device__ __forceinline__ double weight_rt_d(int q) {
     return q == 0 ? 1.0 / 3.0 : (q < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
 }
 
+// Runtime decode / encode of population q of `cell`; local-reference codecs
+// use the cell's reference density ref[cell].
+template <class Codec>
+__device__ __forceinline__ double dec(const typename Codec::S* p, int q, const float* ref, long long cell,
+                                      const DevParams& d) {
+    if constexpr (Codec::kLocal) return Codec::decode_rt(p, weight_rt(q), ref[cell], d);
+    else return decode_rt<Codec>(p, weight_rt(q), d);
+}
+template <class Codec>
+__device__ __forceinline__ void enc(typename Codec::S* p, int q, double v, const float* ref, long long cell,
+                                    const DevParams& d) {
+    if constexpr (Codec::kLocal) Codec::encode_rt(p, weight_rt(q), v, ref[cell], d);
+    else encode_rt<Codec>(p, weight_rt(q), v, d);
+}
+
 template <class Codec>
 __global__ void rest_state_kernel(typename Codec::S* __restrict__ f, const double* __restrict__ rho,
-                                  long long n, DevParams dev) {
+                                  long long n, DevParams dev, float* ref) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const double r = rho[i];
-        for (int q = 0; q < Q; ++q)
-            encode_rt<Codec>(f + q * n + i, weight_rt(q), weight_rt_d(q) * r, dev);
+        if constexpr (Codec::kLocal) ref[i] = float(r);
+        for (int q = 0; q < Q; ++q) enc<Codec>(f + q * n + i, q, weight_rt_d(q) * r, ref, i, dev);
     }
 }
 
 template <class Codec>
 __global__ void ligament_kernel(typename Codec::S* __restrict__ f, int nx, int ny, int nz, double R0,
                                 double eps, int n_waves, double width, double rho_l, double rho_v,
-                                DevParams dev) {
+                                DevParams dev, float* ref) {
     const long long n = (long long)nx * ny * nz;
     const double xc = 0.5 * (nx - 1), yc = 0.5 * (ny - 1);
     const double two_pi = 6.283185307179586476925286766559;
@@ -127,35 +146,54 @@ __global__ void ligament_kernel(typename Codec::S* __restrict__ f, int nx, int n
         const double r = sqrt(dx * dx + dy * dy);
         const double R = R0 * (1.0 + eps * cos(two_pi * n_waves * z / nz));
         const double rho = rho_v + 0.5 * (rho_l - rho_v) * (1.0 - tanh((r - R) / width));
-        for (int q = 0; q < Q; ++q)
-            encode_rt<Codec>(f + q * n + i, weight_rt(q), weight_rt_d(q) * rho, dev);
+        if constexpr (Codec::kLocal) ref[i] = float(rho);
+        for (int q = 0; q < Q; ++q) enc<Codec>(f + q * n + i, q, weight_rt_d(q) * rho, ref, i, dev);
     }
 }
 
 // Element i of `f` belongs to population q0 + i / n.
 template <class Codec>
 __global__ void decode_kernel(double* __restrict__ out, const typename Codec::S* __restrict__ f,
-                              long long count, long long n, int q0, DevParams dev) {
+                              long long count, long long n, int q0, DevParams dev, const float* ref) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
          i += (long long)gridDim.x * blockDim.x)
-        out[i] = decode_rt<Codec>(f + i, weight_rt(q0 + int(i / n)), dev);
+        out[i] = dec<Codec>(f + i, q0 + int(i / n), ref, i % n, dev);
 }
 
 template <class Codec>
 __global__ void encode_kernel(typename Codec::S* __restrict__ f, const double* __restrict__ in,
-                              long long count, long long n, int q0, DevParams dev) {
+                              long long count, long long n, int q0, DevParams dev, const float* ref) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
          i += (long long)gridDim.x * blockDim.x)
-        encode_rt<Codec>(f + i, weight_rt(q0 + int(i / n)), in[i], dev);
+        enc<Codec>(f + i, q0 + int(i / n), in[i], ref, i % n, dev);
+}
+
+// Local-reference codecs: the reference density of a cell given all its
+// populations is their sum.  acc (float64) may be accumulated population by
+// population (add = 1) before ref is set from it (add = 0, in = nullptr).
+__global__ void ref_sum_kernel(float* __restrict__ ref, double* __restrict__ acc, const double* __restrict__ in,
+                               long long n, int count_q, int mode) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (mode == 0) {  // all populations present in `in`
+            double r = 0.0;
+            for (int q = 0; q < count_q; ++q) r += in[q * n + i];
+            ref[i] = float(r);
+        } else if (mode == 1) {  // add one population into acc
+            acc[i] = (count_q == 0 ? 0.0 : acc[i]) + in[i];
+        } else {  // finish: ref from acc
+            ref[i] = float(acc[i]);
+        }
+    }
 }
 
 template <class Codec>
 __global__ void density_kernel(double* __restrict__ rho, const typename Codec::S* __restrict__ f,
-                               long long n, DevParams dev) {
+                               long long n, DevParams dev, const float* ref) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         double r = 0.0;
-        for (int q = 0; q < Q; ++q) r += decode_rt<Codec>(f + q * n + i, weight_rt(q), dev);
+        for (int q = 0; q < Q; ++q) r += dec<Codec>(f + q * n + i, q, ref, i, dev);
         rho[i] = r;
     }
 }
@@ -165,7 +203,7 @@ __global__ void density_kernel(double* __restrict__ rho, const typename Codec::S
 template <class Codec>
 __global__ void velocity_kernel(double* __restrict__ ux, double* __restrict__ uy, double* __restrict__ uz,
                                 const double* __restrict__ rho, const typename Codec::S* __restrict__ f,
-                                int nx, int ny, int nz, double G, double rho0, DevParams dev) {
+                                int nx, int ny, int nz, double G, double rho0, DevParams dev, const float* ref) {
     const long long n = (long long)nx * ny * nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -175,7 +213,7 @@ __global__ void velocity_kernel(double* __restrict__ ux, double* __restrict__ uy
         double jx = 0, jy = 0, jz = 0, sx = 0, sy = 0, sz = 0;
         static_for<0, Q>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
-            const double fq = decode_rt<Codec>(f + q * n + i, float(wq(q)), dev);
+            const double fq = dec<Codec>(f + q * n + i, q, ref, i, dev);
             jx += cx(q) * fq;
             jy += cy(q) * fq;
             jz += cz(q) * fq;
@@ -207,7 +245,7 @@ constexpr int DIAG_THREADS = 256;
 template <class Codec>
 __global__ void __launch_bounds__(DIAG_THREADS)
 diag_kernel(double* __restrict__ out, const typename Codec::S* __restrict__ f, int nx, int ny,
-            long long n, double rho_l, double rho_v, DevParams dev) {
+            long long n, double rho_l, double rho_v, DevParams dev, const float* ref) {
     __shared__ double red[7][DIAG_THREADS];
     const int z = blockIdx.x;
     const long long plane = (long long)nx * ny;
@@ -216,7 +254,9 @@ diag_kernel(double* __restrict__ out, const typename Codec::S* __restrict__ f, i
     const double inv = 1.0 / (rho_l - rho_v);
     for (long long i = threadIdx.x; i < plane; i += DIAG_THREADS) {
         double r, ax, ay, az;
-        diag_cell<Codec>(fz + i, n, dev, r, ax, ay, az);
+        float rf = 0.0f;
+        if constexpr (Codec::kLocal) rf = ref[z * plane + i];
+        diag_cell<Codec>(fz + i, n, dev, r, ax, ay, az, rf);
         m += r;
         jx += ax;
         jy += ay;
@@ -259,6 +299,7 @@ StepLaunch step_launch(const lbm_ctx* c) {
     StepLaunch l;
     l.args = c->args;
     l.kernel = c->kernel;
+    l.tmap = nullptr;
     l.tile_y = c->tile_y;
     l.grid = c->grid;
     l.coll = c->coll;
@@ -272,7 +313,48 @@ int prepare_async(lbm_ctx* c) {
 }
 
 cudaError_t launch_step(const lbm_ctx* c, const void* src, void* dst) {
-    return step_kernels(c->p.storage, c->coll).launch(step_launch(c), src, dst);
+    StepLaunch l = step_launch(c);
+    if (c->kernel == 5) {
+        const int idx = src == c->f[0] ? 0 : (src == c->f[1] ? 1 : -1);
+        if (idx >= 0) {
+            l.tmap = &c->tmap[idx];
+        } else {  // other buffers (adjoint segments): the pipelined kernel
+            l.kernel = 3;
+            l.grid = c->grid3;
+        }
+    }
+    if (c->ref[0]) {  // local-reference storage: the density fields follow their population copies
+        const int k = src == c->f[0] ? 0 : 1;
+        l.args.ref_src = c->ref[k];
+        l.args.ref_dst = c->ref[k ^ 1];
+    }
+    return step_kernels(c->p.storage, c->coll).launch(l, src, dst);
+}
+
+// Tensor maps of the two population copies for the tensor-copy kernel:
+// 4-D (x, y, z, population), FP32, box 32 x tile_y x 1 x 19.
+lbm_status encode_tensor_maps(lbm_ctx* c) {
+    using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || !fn || q != cudaDriverEntryPointSuccess)
+        return c->fail(LBM_ECUDA, "cuTensorMapEncodeTiled is not available");
+    const cuuint64_t nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
+    const cuuint64_t dims[4] = {nx, ny, nz, (cuuint64_t)Q};
+    const cuuint64_t strides[3] = {nx * 4, nx * ny * 4, nx * ny * nz * 4};
+    const cuuint32_t box[4] = {32, (cuuint32_t)c->tile_y, 1, (cuuint32_t)Q};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    for (int k = 0; k < 2; ++k) {
+        CUresult r = reinterpret_cast<EncodeFn>(fn)(&c->tmap[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->f[k], dims,
+                                                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return c->fail(LBM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
+    }
+    return LBM_OK;
 }
 
 // Collision kernel for the operator and rates: the MRT specialisations are
@@ -298,6 +380,8 @@ auto with_codec(const lbm_ctx* c, Fn&& fn) {
         case LBM_F64: return fn(CodecF64{});
         case LBM_F16_DEV: return fn(CodecF16Dev{});
         case LBM_BF16_DEV: return fn(CodecBF16Dev{});
+        case LBM_F16_LOCAL: return fn(CodecF16Local{});
+        case LBM_BF16_LOCAL: return fn(CodecBF16Local{});
         default: return fn(CodecF32{});
     }
 }
@@ -399,9 +483,11 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     if (!std::isfinite(p->G)) return create_fail(LBM_EINVAL, "lbm_create: G must be finite");
     if (p->psi != LBM_PSI_EXP) return create_fail(LBM_EINVAL, "lbm_create: unknown psi law");
     if (!(p->rho0 > 0) || !std::isfinite(p->rho0)) return create_fail(LBM_EINVAL, "lbm_create: rho0 must be > 0");
-    if (p->storage < LBM_F64 || p->storage > LBM_BF16_DEV) return create_fail(LBM_EINVAL, "lbm_create: unknown storage");
+    if (p->storage < LBM_F64 || p->storage > LBM_BF16_LOCAL) return create_fail(LBM_EINVAL, "lbm_create: unknown storage");
     if (p->storage >= LBM_F16_DEV && (!(p->dev_scale > 0) || !std::isfinite(p->rho_ref)))
         return create_fail(LBM_EINVAL, "lbm_create: deviation storage needs dev_scale > 0 and finite rho_ref");
+    if (p->storage >= LBM_F16_LOCAL && p->kernel > 1)
+        return create_fail(LBM_EINVAL, "lbm_create: local-reference storage runs kernel 1 only");
     if (p->collision == LBM_MRT_GUO && p->has_rates) {
         for (int k = 0; k < Q; ++k)
             if (!(p->s[k] > 0.0 && p->s[k] < 2.0))
@@ -447,9 +533,29 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
         cudaMemsetAsync(c->f[0], 0, fbytes, c->stream);
         cudaMemsetAsync(c->f[1], 0, fbytes, c->stream);
     }
+    if (p->storage >= LBM_F16_LOCAL) {
+        // the two density fields are the library's own even with caller-owned populations
+        const size_t rbytes = sizeof(float) * (size_t)n;
+        e = cudaMalloc(&c->ref[0], rbytes);
+        if (e == cudaSuccess) e = cudaMalloc(&c->ref[1], rbytes);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->ref[0], 0, rbytes, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->ref[1], 0, rbytes, c->stream);
+        if (e != cudaSuccess) {
+            snprintf(g_create_err, sizeof(g_create_err), "lbm_create: density-field allocation failed: %s",
+                     cudaGetErrorString(e));
+            cudaFree(c->ref[0]);
+            cudaFree(c->ref[1]);
+            if (c->own_f) { cudaFree(c->f[0]); cudaFree(c->f[1]); }
+            delete c;
+            return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+        }
+        c->own_bytes += 2 * (long long)rbytes;
+    }
     e = cudaMalloc(&c->diag, sizeof(double) * 8 * (size_t)p->nz);
     if (e != cudaSuccess) {
         snprintf(g_create_err, sizeof(g_create_err), "lbm_create: diagnostics allocation failed: %s", cudaGetErrorString(e));
+        cudaFree(c->ref[0]);
+        cudaFree(c->ref[1]);
         if (c->own_f) { cudaFree(c->f[0]); cudaFree(c->f[1]); }
         delete c;
         return LBM_ENOMEM;
@@ -462,6 +568,8 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
         snprintf(g_create_err, sizeof(g_create_err), "lbm_create: error-word allocation failed: %s",
                  cudaGetErrorString(e));
         cudaFree(c->diag);
+        cudaFree(c->ref[0]);
+        cudaFree(c->ref[1]);
         if (c->own_f) { cudaFree(c->f[0]); cudaFree(c->f[1]); }
         delete c;
         return LBM_ENOMEM;
@@ -502,14 +610,20 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     const bool pipe_default = p->storage == LBM_F32;
     const int coll = c->coll;
     const bool wide = (coll == COLL_SRT || coll == COLL_MRT_UNIT) && (p->kernel == 3 || (p->kernel == 0 && pipe_default));
-    c->tile_y = p->tile_y ? p->tile_y : (wide ? 16 : 4);
+    c->tile_y = p->tile_y ? p->tile_y : ((wide || p->kernel == 5) ? 16 : 4);
     if (p->kernel == 4 && (p->storage != LBM_F32 || p->nx % 4 != 0)) {
         snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel 4 needs FP32 storage and nx %% 4 == 0");
         lbm_destroy(c);
         return LBM_EINVAL;
     }
-    if (p->kernel < 0 || p->kernel > 4) {
-        snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel must be 0, 1, 2, 3 or 4");
+    if (p->kernel == 5 && (p->storage != LBM_F32 || c->tile_y < 8 || p->nx % 32 != 0 || p->ny % c->tile_y != 0)) {
+        snprintf(g_create_err, sizeof(g_create_err),
+                 "lbm_create: kernel 5 needs FP32 storage, tile_y 8 or 16, nx %% 32 == 0 and ny %% tile_y == 0");
+        lbm_destroy(c);
+        return LBM_EINVAL;
+    }
+    if (p->kernel < 0 || p->kernel > 5) {
+        snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel must be 0 .. 5");
         lbm_destroy(c);
         return LBM_EINVAL;
     }
@@ -534,6 +648,18 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
             c->kernel = 1;
         }
     }
+    if (c->kernel == 5) {
+        c->kernel = 3;
+        const int per3 = prepare_async(c);
+        c->kernel = 5;
+        if (per3 < 1 || encode_tensor_maps(c) != LBM_OK) {
+            snprintf(g_create_err, sizeof(g_create_err), "lbm_create: %s",
+                     c->err[0] ? c->err : "the pipelined kernel cannot be configured");
+            lbm_destroy(c);
+            return LBM_ECUDA;
+        }
+        c->grid3 = per3 * c->num_sms;
+    }
     const int tiles_x = (p->nx + 31) / 32, tiles_y = (p->ny + c->tile_y - 1) / c->tile_y;
     if (p->zchunk) {
         c->zchunk = p->zchunk < p->nz ? p->zchunk : p->nz;
@@ -552,6 +678,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     a.n_tiles = tiles_x * tiles_y;
     a.n_items = a.n_tiles * ((p->nz + c->zchunk - 1) / c->zchunk);
     if (c->kernel >= 2 && c->grid > a.n_items) c->grid = a.n_items;
+    if (c->grid3 > a.n_items) c->grid3 = a.n_items;
 
     e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -570,6 +697,8 @@ void lbm_destroy(lbm_ctx* c) {
         cudaFree(c->f[0]);
         cudaFree(c->f[1]);
     }
+    cudaFree(c->ref[0]);
+    cudaFree(c->ref[1]);
     cudaFree(c->scratch);
     cudaFree(c->diag);
     cudaFree(c->dev_err);
@@ -623,7 +752,8 @@ lbm_status lbm_init_ligament(lbm_ctx* c, double R0, double eps, int n_waves, dou
     with_codec(c, [&](auto codec) {
         using C = decltype(codec);
         ligament_kernel<C><<<blocks, 256, 0, c->stream>>>(static_cast<typename C::S*>(c->f[c->cur]), p.nx, p.ny,
-                                                          p.nz, R0, eps, n_waves, width, rho_l, rho_v, c->args.dev);
+                                                          p.nz, R0, eps, n_waves, width, rho_l, rho_v, c->args.dev,
+                                                          c->ref[c->cur]);
         return 0;
     });
     LBM_LAUNCHED(c, "ligament_kernel");
@@ -645,7 +775,7 @@ lbm_status lbm_set_density(lbm_ctx* c, const double* rho, int on_device) {
     with_codec(c, [&](auto codec) {
         using C = decltype(codec);
         rest_state_kernel<C><<<blocks, 256, 0, c->stream>>>(static_cast<typename C::S*>(c->f[c->cur]), d_rho, c->n,
-                                                            c->args.dev);
+                                                            c->args.dev, c->ref[c->cur]);
         return 0;
     });
     LBM_LAUNCHED(c, "rest_state_kernel");
@@ -657,19 +787,32 @@ lbm_status lbm_set_density(lbm_ctx* c, const double* rho, int on_device) {
 lbm_status lbm_set_populations(lbm_ctx* c, const double* f, int on_device) {
     if (!c) return LBM_EINVAL;
     if (!f) return c->fail(LBM_EINVAL, "lbm_set_populations: f is NULL");
+    float* ref = c->ref[c->cur];
+    const int blocks = grid_for(c->n, 256, c->num_sms);
     if (on_device) {
+        if (ref) ref_sum_kernel<<<blocks, 256, 0, c->stream>>>(ref, nullptr, f, c->n, Q, 0);
         with_codec(c, [&](auto codec) {
             using C = decltype(codec);
             encode_kernel<C><<<grid_for((long long)Q * c->n, 256, c->num_sms), 256, 0, c->stream>>>(
-                static_cast<typename C::S*>(c->f[c->cur]), f, (long long)Q * c->n, c->n, 0, c->args.dev);
+                static_cast<typename C::S*>(c->f[c->cur]), f, (long long)Q * c->n, c->n, 0, c->args.dev, ref);
             return 0;
         });
         LBM_LAUNCHED(c, "encode_kernel");
     } else {
-        // One population at a time through an n-double staging buffer.
-        lbm_status s = ensure_scratch(c, sizeof(double) * (size_t)c->n);
+        // One population at a time through an n-double staging buffer (plus
+        // an n-double accumulator of the reference densities for the
+        // local-reference storage, which needs them before the first encode).
+        lbm_status s = ensure_scratch(c, sizeof(double) * (size_t)c->n * (ref ? 2 : 1));
         if (s != LBM_OK) return s;
-        const int blocks = grid_for(c->n, 256, c->num_sms);
+        if (ref) {
+            for (int q = 0; q < Q; ++q) {
+                LBM_CUDA(c, cudaMemcpyAsync(c->scratch, f + (size_t)q * c->n, sizeof(double) * (size_t)c->n,
+                                            cudaMemcpyHostToDevice, c->stream));
+                ref_sum_kernel<<<blocks, 256, 0, c->stream>>>(ref, c->scratch + c->n, c->scratch, c->n, q, 1);
+            }
+            ref_sum_kernel<<<blocks, 256, 0, c->stream>>>(ref, c->scratch + c->n, nullptr, c->n, Q, 2);
+            LBM_LAUNCHED(c, "ref_sum_kernel");
+        }
         for (int q = 0; q < Q; ++q) {
             LBM_CUDA(c, cudaMemcpyAsync(c->scratch, f + (size_t)q * c->n, sizeof(double) * (size_t)c->n,
                                         cudaMemcpyHostToDevice, c->stream));
@@ -677,7 +820,7 @@ lbm_status lbm_set_populations(lbm_ctx* c, const double* f, int on_device) {
                 using C = decltype(codec);
                 encode_kernel<C><<<blocks, 256, 0, c->stream>>>(
                     static_cast<typename C::S*>(c->f[c->cur]) + (size_t)q * c->n, c->scratch, c->n, c->n, q,
-                    c->args.dev);
+                    c->args.dev, ref);
                 return 0;
             });
             LBM_LAUNCHED(c, "encode_kernel");
@@ -696,7 +839,8 @@ lbm_status lbm_get_populations(lbm_ctx* c, double* f, int on_device) {
         with_codec(c, [&](auto codec) {
             using C = decltype(codec);
             decode_kernel<C><<<grid_for((long long)Q * c->n, 256, c->num_sms), 256, 0, c->stream>>>(
-                f, static_cast<const typename C::S*>(c->f[c->cur]), (long long)Q * c->n, c->n, 0, c->args.dev);
+                f, static_cast<const typename C::S*>(c->f[c->cur]), (long long)Q * c->n, c->n, 0, c->args.dev,
+                c->ref[c->cur]);
             return 0;
         });
         LBM_LAUNCHED(c, "decode_kernel");
@@ -710,7 +854,7 @@ lbm_status lbm_get_populations(lbm_ctx* c, double* f, int on_device) {
             using C = decltype(codec);
             decode_kernel<C><<<blocks, 256, 0, c->stream>>>(
                 c->scratch, static_cast<const typename C::S*>(c->f[c->cur]) + (size_t)q * c->n, c->n, c->n, q,
-                c->args.dev);
+                c->args.dev, c->ref[c->cur]);
             return 0;
         });
         LBM_LAUNCHED(c, "decode_kernel");
@@ -759,10 +903,10 @@ lbm_status lbm_moments(lbm_ctx* c, double* rho, double* ux, double* uy, double* 
     with_codec(c, [&](auto codec) {
         using C = decltype(codec);
         const auto* f = static_cast<const typename C::S*>(c->f[c->cur]);
-        density_kernel<C><<<blocks, 256, 0, c->stream>>>(d_rho, f, c->n, c->args.dev);
+        density_kernel<C><<<blocks, 256, 0, c->stream>>>(d_rho, f, c->n, c->args.dev, c->ref[c->cur]);
         if (d_ux || d_uy || d_uz)
             velocity_kernel<C><<<blocks, 256, 0, c->stream>>>(d_ux, d_uy, d_uz, d_rho, f, p.nx, p.ny, p.nz, p.G,
-                                                              p.rho0, c->args.dev);
+                                                              p.rho0, c->args.dev, c->ref[c->cur]);
         return 0;
     });
     LBM_LAUNCHED(c, "moments kernels");
@@ -785,7 +929,8 @@ lbm_status lbm_diag(lbm_ctx* c, double rho_l, double rho_v, double* mass, double
     with_codec(c, [&](auto codec) {
         using C = decltype(codec);
         diag_kernel<C><<<p.nz, DIAG_THREADS, 0, c->stream>>>(
-            c->diag, static_cast<const typename C::S*>(c->f[c->cur]), p.nx, p.ny, c->n, rho_l, rho_v, c->args.dev);
+            c->diag, static_cast<const typename C::S*>(c->f[c->cur]), p.nx, p.ny, c->n, rho_l, rho_v, c->args.dev,
+            c->ref[c->cur]);
         return 0;
     });
     LBM_LAUNCHED(c, "diag_kernel");

@@ -2,6 +2,7 @@
 // the host API (lbm_sc.cu) and the per-storage kernel translation units
 // (step_f64.cu, step_f32.cu, step_f16.cu, step_bf16.cu).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "codec.cuh"
@@ -25,6 +26,8 @@ struct StepArgs {
     double s[Q];          // MRT rates, moment order
     DevParams dev;
     int* err;             // device error word (bit 0: a bounded wait timed out)
+    const float* ref_src; // local-reference storage: density field of the source copy
+    float* ref_dst;       // ... and of the destination copy
     int test_stall;       // failure test of the bounded waits (bulk kernel)
 };
 
@@ -47,7 +50,9 @@ struct BatchArgs {
 // Launch description of one step.
 struct StepLaunch {
     StepArgs args;
-    int kernel;           // 1 register-staged, 2 cp.async-staged, 3 pipelined
+    int kernel;           // 1 register-staged, 2 cp.async-staged, 3 pipelined,
+                          // 4 bulk-copy, 5 tensor-copy
+    const CUtensorMap* tmap;  // kernel 5: tensor map of the source copy
     int tile_y;           // 4, 8 or 16 (tile width is 32)
     int grid;             // persistent grid (kernels 2 and 3)
     int coll;             // COLL_SRT .. COLL_MRT_UNIT
@@ -66,7 +71,7 @@ struct StepKernels {
     int (*batch_prepare)(const StepLaunch& l);
 };
 
-// storage: LBM_F64 .. LBM_BF16_DEV (0..3); coll: COLL_SRT .. COLL_MRT_UNIT.
+// storage: LBM_F64 .. LBM_BF16_LOCAL (0..5); coll: COLL_SRT .. COLL_MRT_UNIT.
 const StepKernels& step_kernels(int storage, int coll);
 
 }  // namespace lbm

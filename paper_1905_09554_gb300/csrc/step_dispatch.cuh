@@ -17,6 +17,13 @@ cudaError_t launch_step_t(const StepLaunch& c, const void* src, void* dst) {
                 static_cast<const float*>(src), static_cast<float*>(dst), a);
             return cudaGetLastError();
         }
+        if constexpr (TY >= 8) {
+            if (c.kernel == 5) {
+                sc_step_tma_kernel<COLL, TY><<<c.grid, 32 * TY, TmaLayout<TY>::bytes, c.stream>>>(
+                    *c.tmap, static_cast<const float*>(src), static_cast<float*>(dst), a);
+                return cudaGetLastError();
+            }
+        }
     }
     if constexpr (sizeof(typename Codec::S) >= 4) {
         if (c.kernel == 3) {
@@ -42,6 +49,16 @@ cudaError_t launch_step_t(const StepLaunch& c, const void* src, void* dst) {
 template <class Codec, int COLL, int TY>
 int prepare_async_t(const StepLaunch& c) {
     constexpr int TX = 32;
+    if constexpr (std::is_same_v<Codec, CodecF32> && TY >= 8) {
+        if (c.kernel == 5) {
+            auto kern = sc_step_tma_kernel<COLL, TY>;
+            const int sm = (int)TmaLayout<TY>::bytes;
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            int per_sm = 0;
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * TY, sm);
+            return e == cudaSuccess ? per_sm : -int(e);
+        }
+    }
     if constexpr (std::is_same_v<Codec, CodecF32>) {
         if (c.kernel == 4) {
             auto kern = sc_step_bulk_kernel<COLL, TY>;

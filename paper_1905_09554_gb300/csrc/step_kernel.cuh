@@ -19,6 +19,8 @@
 // HBM traffic per cell update is therefore one read and one write of the 19
 // populations plus the halo/chunk re-reads that miss L2.
 #pragma once
+#include <cuda.h>
+
 #include <cstdint>
 
 #include "codec.cuh"
@@ -279,12 +281,13 @@ __device__ __forceinline__ void collide_mrt_sparse(R (&f)[Q], R Fx, R Fy, R Fz, 
 
 template <class Codec>
 __device__ __forceinline__ typename Codec::R cell_density(const typename Codec::S* __restrict__ p,
-                                                          long long n, const DevParams& dev) {
+                                                          long long n, const DevParams& dev, float ref = 0.0f) {
     using R = typename Codec::R;
     R r = R(0);
     static_for<0, Q>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
-        r += Codec::template load<q>(p + q * n, dev);
+        if constexpr (Codec::kLocal) r += Codec::template load_ref<q>(p + q * n, ref, dev);
+        else r += Codec::template load<q>(p + q * n, dev);
     });
     return r;
 }
@@ -296,7 +299,8 @@ __device__ __forceinline__ void update_cell(typename Codec::R (&fc)[Q], const ty
                                             const typename Codec::R* p0, const typename Codec::R* pp,
                                             int slot, typename Codec::S* __restrict__ dst, I n,
                                             const I (&zoff)[3], const I (&yoff)[3],
-                                            const int (&xidx)[3], const StepArgs& a) {
+                                            const int (&xidx)[3], const StepArgs& a,
+                                            const float* const* rho_pl = nullptr) {
     using R = typename Codec::R;
     const R* pl[3] = {pm, p0, pp};
     // Eq. SC_force: F = -G psi(x) sum_a w_a psi(x + c_a) c_a.
@@ -320,7 +324,13 @@ __device__ __forceinline__ void update_cell(typename Codec::R (&fc)[Q], const ty
     static_for<0, Q>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         const I idx = zoff[cz(q) + 1] + yoff[cy(q) + 1] + xidx[cx(q) + 1];
-        Codec::template store<q>(dst + (I(q) * n + idx), fc[q], a.dev);
+        if constexpr (Codec::kLocal) {
+            // deviation from the rest equilibrium at the destination's density
+            const float ref = rho_pl[cz(q) + 1][slot + cx(q) + cy(q) * PX];
+            Codec::template store_ref<q>(dst + (I(q) * n + idx), fc[q], ref, a.dev);
+        } else {
+            Codec::template store<q>(dst + (I(q) * n + idx), fc[q], a.dev);
+        }
     });
 }
 
@@ -333,6 +343,9 @@ sc_step_kernel(const typename Codec::S* __restrict__ src, typename Codec::S* __r
     constexpr int NHALO = 2 * PX + 2 * TY;
     static_assert(NHALO <= TX * TY, "tile too small for its halo ring");
     __shared__ R psi_s[NSLOT][PLANE];
+    // local-reference storage: densities of the same planes (encode targets)
+    constexpr bool LOCAL = Codec::kLocal;
+    __shared__ float rho_s[LOCAL ? NSLOT : 1][LOCAL ? PLANE : 1];
 
     const int tid = threadIdx.x;
     const int lx = tid % TX, ly = tid / TX;
@@ -372,30 +385,49 @@ sc_step_kernel(const typename Codec::S* __restrict__ src, typename Codec::S* __r
     const DevParams dev = a.dev;
 
     auto slot_of = [&](int z) { return (z - zs + 1) & (NSLOT - 1); };
+    auto ref_at = [&](long long cell) -> float {
+        if constexpr (LOCAL) return __ldg(a.ref_src + cell);
+        else return 0.0f;
+    };
+    auto put_rho = [&](int slot, int idx, R r) {
+        if constexpr (LOCAL) rho_s[slot][idx] = r;
+    };
+    auto load_q = [&](auto qc, const typename Codec::S* p, float ref) {
+        constexpr int q = decltype(qc)::value;
+        if constexpr (LOCAL) return Codec::template load_ref<q>(p, ref, dev);
+        else return Codec::template load<q>(p, dev);
+    };
 
     // Prologue: psi of plane zs-1, then populations and psi of plane zs.
     {
         const int zm = (zs == 0) ? nz - 1 : zs - 1;
         const long long zo = (long long)zm * plane;
-        psi_s[slot_of(zs - 1)][my_slot] =
-            psi_of<R>(cell_density<Codec>(src + zo + my_xy, n, dev), rho0, inv_rho0);
-        if (h_slot >= 0)
-            psi_s[slot_of(zs - 1)][h_slot] =
-                psi_of<R>(cell_density<Codec>(src + zo + h_xy, n, dev), rho0, inv_rho0);
+        const R r = cell_density<Codec>(src + zo + my_xy, n, dev, ref_at(zo + my_xy));
+        psi_s[slot_of(zs - 1)][my_slot] = psi_of<R>(r, rho0, inv_rho0);
+        put_rho(slot_of(zs - 1), my_slot, r);
+        if (h_slot >= 0) {
+            const R rh = cell_density<Codec>(src + zo + h_xy, n, dev, ref_at(zo + h_xy));
+            psi_s[slot_of(zs - 1)][h_slot] = psi_of<R>(rh, rho0, inv_rho0);
+            put_rho(slot_of(zs - 1), h_slot, rh);
+        }
     }
     R fc[Q];
     {
         const long long zo = (long long)zs * plane;
+        const float ref = ref_at(zo + my_xy);
         R r = R(0);
         static_for<0, Q>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
-            fc[q] = Codec::template load<q>(src + q * n + zo + my_xy, dev);
+            fc[q] = load_q(qc, src + q * n + zo + my_xy, ref);
             r += fc[q];
         });
         psi_s[slot_of(zs)][my_slot] = psi_of<R>(r, rho0, inv_rho0);
-        if (h_slot >= 0)
-            psi_s[slot_of(zs)][h_slot] =
-                psi_of<R>(cell_density<Codec>(src + zo + h_xy, n, dev), rho0, inv_rho0);
+        put_rho(slot_of(zs), my_slot, r);
+        if (h_slot >= 0) {
+            const R rh = cell_density<Codec>(src + zo + h_xy, n, dev, ref_at(zo + h_xy));
+            psi_s[slot_of(zs)][h_slot] = psi_of<R>(rh, rho0, inv_rho0);
+            put_rho(slot_of(zs), h_slot, rh);
+        }
     }
 
     for (int z = zs; z < ze; ++z) {
@@ -404,24 +436,35 @@ sc_step_kernel(const typename Codec::S* __restrict__ src, typename Codec::S* __r
         R fn[Q];
         {
             const long long zo = (long long)zn * plane;
+            const float ref = ref_at(zo + my_xy);
             R r = R(0);
             static_for<0, Q>([&](auto qc) {
                 constexpr int q = decltype(qc)::value;
-                fn[q] = Codec::template load<q>(src + q * n + zo + my_xy, dev);
+                fn[q] = load_q(qc, src + q * n + zo + my_xy, ref);
                 r += fn[q];
             });
             psi_s[zp_slot][my_slot] = psi_of<R>(r, rho0, inv_rho0);
-            if (h_slot >= 0)
-                psi_s[zp_slot][h_slot] =
-                    psi_of<R>(cell_density<Codec>(src + zo + h_xy, n, dev), rho0, inv_rho0);
+            put_rho(zp_slot, my_slot, r);
+            if (h_slot >= 0) {
+                const R rh = cell_density<Codec>(src + zo + h_xy, n, dev, ref_at(zo + h_xy));
+                psi_s[zp_slot][h_slot] = psi_of<R>(rh, rho0, inv_rho0);
+                put_rho(zp_slot, h_slot, rh);
+            }
         }
         __syncthreads();
 
         if (active) {
             const int zm = (z == 0) ? nz - 1 : z - 1;
             const long long zoff[3] = {(long long)zm * plane, (long long)z * plane, (long long)zn * plane};
-            update_cell<Codec, COLL, PX>(fc, psi_s[slot_of(z - 1)], psi_s[slot_of(z)], psi_s[zp_slot], my_slot,
-                                         dst, n, zoff, yoff, xidx, a);
+            if constexpr (LOCAL) {
+                const float* rp[3] = {rho_s[slot_of(z - 1)], rho_s[slot_of(z)], rho_s[zp_slot]};
+                update_cell<Codec, COLL, PX>(fc, psi_s[slot_of(z - 1)], psi_s[slot_of(z)], psi_s[zp_slot], my_slot,
+                                             dst, n, zoff, yoff, xidx, a, rp);
+                a.ref_dst[zoff[1] + my_xy] = rho_s[slot_of(z)][my_slot];  // this cell's density now
+            } else {
+                update_cell<Codec, COLL, PX>(fc, psi_s[slot_of(z - 1)], psi_s[slot_of(z)], psi_s[zp_slot], my_slot,
+                                             dst, n, zoff, yoff, xidx, a);
+            }
         }
         static_for<0, Q>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
@@ -1017,6 +1060,183 @@ sc_step_bulk_kernel(const float* __restrict__ src, float* __restrict__ dst, cons
         release(g0 + (ze - zs) + 1);  // plane ze: psi only
         g = g0 + (ze - zs) + 2;
     }
+}
+
+// ----------------------------------------------------------------------------
+// Tensor-copy variant (FP32 storage, nx a multiple of 32, ny a multiple of
+// TY).
+//
+// The pipelined kernel's 19 loads per cell and plane become ONE
+// cp.async.bulk.tensor.4d copy per plane of the tile's cells (box
+// 32 x TY x 1 x 19 of the 4-D tensor map (x, y, z, population)), issued by a
+// single thread into a four-stage shared-memory buffer three planes ahead
+// and completing on an mbarrier per stage.  Tile boxes never leave the box of
+// the lattice, so the tensor map's zero fill is never used; the one-cell ring
+// (with its periodic wrap) keeps the four-stage 4/8-byte cp.async buffer of
+// the pipelined kernel.  All threads compute; the per-plane barrier also
+// marks the stage three planes back as free.  mbarrier waits are bounded as
+// in the bulk-copy variant.
+// ----------------------------------------------------------------------------
+template <int TY>
+struct TmaLayout {
+    static constexpr int TX = 32;
+    static constexpr int NT = TX * TY;
+    static constexpr int NHALO = 2 * (TX + 2) + 2 * TY;
+    static constexpr int PX = TX + 2;
+    static constexpr int PLANE = PX * (TY + 2);
+    static constexpr int NSTAGE = 4;
+    static constexpr unsigned stage_floats = Q * NT;
+    static constexpr unsigned stage_bytes = stage_floats * 4;
+    static constexpr size_t bytes =
+        NSTAGE * (size_t)stage_bytes + NSTAGE * (size_t)Q * NHALO * 4 + 4 * (size_t)PLANE * 4 + NSTAGE * 8;
+};
+
+namespace tma {
+__device__ __forceinline__ void load_box(float* dst, const CUtensorMap* map, int x, int y, int z,
+                                         unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];\n" ::"r"(bulk::smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(0), "r"(bulk::smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+}  // namespace tma
+
+template <int COLL, int TY>
+__global__ void __launch_bounds__(32 * TY, (TY >= 16) ? 1 : 2)
+sc_step_tma_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict__ src, float* __restrict__ dst,
+                   const StepArgs a) {
+    using L = TmaLayout<TY>;
+    using R = float;
+    constexpr int TX = L::TX, NT = L::NT, NH = L::NHALO, PX = L::PX, PLANE = L::PLANE, NS = L::NSTAGE;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float* istage = reinterpret_cast<float*>(smem_raw);             // [NS][Q][TY][TX]
+    float* hstage = istage + NS * L::stage_floats;                 // [NS][Q][NH]
+    float* ring = hstage + NS * Q * NH;                             // [4][PLANE]
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(ring + 4 * PLANE);
+
+    const int tid = threadIdx.x;
+    const int lx = tid % TX, ly = tid / TX;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const long long n = a.n;
+    const long long plane = (long long)nx * ny;
+    const R rho0 = R(a.rho0), inv_rho0 = R(a.inv_rho0);
+    const int my_slot = (ly + 1) * PX + (lx + 1);
+    const int my_st = ly * TX + lx;
+    bool bad = false;
+
+    constexpr int NW = NT / 32, HC = (NH + NW - 1) / NW;
+    static_assert(HC <= 32, "ring run longer than a warp");
+    int hx = 0, hy = 0, h_slot = -1;
+    const int h = (tid / 32) * HC + (tid % 32);
+    if ((tid % 32) < HC && h < NH) {
+        if (h < PX) { hx = h - 1; hy = -1; }
+        else if (h < 2 * PX) { hx = h - PX - 1; hy = TY; }
+        else { const int k = h - 2 * PX; hx = (k < TY) ? -1 : TX; hy = (k < TY) ? k : k - TY; }
+        h_slot = (hy + 1) * PX + (hx + 1);
+    }
+
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) bulk::bar_init(&full[s], 1);
+        bulk::fence_init();
+    }
+    __syncthreads();
+
+    unsigned g = 0;  // planes issued so far by this block
+    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+        const int tile = item % a.n_tiles, chunk = item / a.n_tiles;
+        const int x0 = (tile % a.tiles_x) * TX, y0 = (tile / a.tiles_x) * TY;
+        const int zs = chunk * a.zchunk, ze = min(zs + a.zchunk, nz);
+        const int gx = x0 + lx, gy = y0 + ly;
+        const long long h_xy =
+            (h_slot >= 0) ? (long long)wrap_index(y0 + hy, ny) * nx + wrap_index(x0 + hx, nx) : 0;
+        const int xp = (gx + 1 == nx) ? 0 : gx + 1, xm = (gx == 0) ? nx - 1 : gx - 1;
+        const int yp = (gy + 1 == ny) ? 0 : gy + 1, ym = (gy == 0) ? ny - 1 : gy - 1;
+        const long long yoff[3] = {(long long)ym * nx, (long long)gy * nx, (long long)yp * nx};
+        const int xidx[3] = {xm, gx, xp};
+        const unsigned g0 = g;  // plane p of this item has index g0 + (p - zs + 1)
+        auto wrapz = [&](int z) { return z < 0 ? z + nz : (z >= nz ? z - nz : z); };
+        auto gi_of = [&](int p) { return g0 + unsigned(p - zs + 1); };
+        auto slot_of = [&](int z) { return (z - zs + 1) & 3; };
+        auto issue = [&](int p) {  // plane p: tensor box (one thread) + ring copies; one cp.async group
+            const unsigned gi = gi_of(p);
+            const int s = gi % NS;
+            const int zw = wrapz(p);
+            if (tid == 0) {
+                tma::fence_proxy_async();
+                bulk::arrive_expect_tx(&full[s], L::stage_bytes);
+                tma::load_box(istage + s * L::stage_floats, &tmap, x0, y0, zw, &full[s]);
+            }
+            if (h_slot >= 0) {
+                const float* base = src + (long long)zw * plane + h_xy;
+                float* st = hstage + s * (Q * NH);
+                static_for<0, Q>([&](auto qc) {
+                    constexpr int q = decltype(qc)::value;
+                    async_copy::copy<4>(st + q * NH + h, base + q * n);
+                });
+            }
+            async_copy::commit();
+        };
+        auto wait_box = [&](int p) {
+            const unsigned gi = gi_of(p);
+            bulk::wait(&full[gi % NS], (gi / NS) & 1, bad, a.err);
+        };
+        auto psi_from = [&](int p) {
+            const int s = gi_of(p) % NS;
+            const float* st = istage + s * L::stage_floats;
+            R r = R(0);
+            static_for<0, Q>([&](auto qc) {
+                constexpr int q = decltype(qc)::value;
+                r += st[q * NT + my_st];
+            });
+            ring[slot_of(p) * PLANE + my_slot] = psi_of<R>(r, rho0, inv_rho0);
+            if (h_slot >= 0) {
+                const float* hs = hstage + s * (Q * NH);
+                R rh = R(0);
+                static_for<0, Q>([&](auto qc) {
+                    constexpr int q = decltype(qc)::value;
+                    rh += hs[q * NH + h];
+                });
+                ring[slot_of(p) * PLANE + h_slot] = psi_of<R>(rh, rho0, inv_rho0);
+            }
+        };
+
+        __syncthreads();  // the previous item is finished with every stage and the psi ring
+        // prologue: planes zs-1 .. zs+2 (four cp.async groups, empty ones past ze)
+        for (int p = zs - 1; p <= zs + 2; ++p) {
+            if (p <= ze) issue(p);
+            else async_copy::commit();
+        }
+        async_copy::wait<3>();
+        wait_box(zs - 1);
+        psi_from(zs - 1);
+        async_copy::wait<2>();
+        wait_box(zs);
+        psi_from(zs);
+        for (int z = zs; z < ze; ++z) {
+            async_copy::wait<1>();
+            wait_box(z + 1);
+            psi_from(z + 1);
+            __syncthreads();
+            // every thread is past plane z-1: its stage takes plane z+3
+            if (z + 3 <= ze) issue(z + 3);
+            else async_copy::commit();
+            const float* st = istage + (gi_of(z) % NS) * L::stage_floats;
+            R fc[Q];
+            static_for<0, Q>([&](auto qc) {
+                constexpr int q = decltype(qc)::value;
+                fc[q] = st[q * NT + my_st];
+            });
+            const int zm = (z == 0) ? nz - 1 : z - 1;
+            const int zn = (z + 1 == nz) ? 0 : z + 1;
+            const long long zoff[3] = {(long long)zm * plane, (long long)z * plane, (long long)zn * plane};
+            update_cell<CodecF32, COLL, PX>(fc, ring + slot_of(z - 1) * PLANE, ring + slot_of(z) * PLANE,
+                                            ring + slot_of(z + 1) * PLANE, my_slot, dst, n, zoff, yoff, xidx, a);
+        }
+        g = g0 + unsigned(ze - zs + 2);
+    }
+    async_copy::wait<0>();
 }
 
 }  // namespace lbm

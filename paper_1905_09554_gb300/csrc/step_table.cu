@@ -19,13 +19,23 @@ extern const StepKernels kStep_bf16_srt;
 extern const StepKernels kStep_bf16_mrt;
 extern const StepKernels kStep_bf16_mrts;
 extern const StepKernels kStep_bf16_mrtu;
+extern const StepKernels kStep_f16l_srt;
+extern const StepKernels kStep_f16l_mrt;
+extern const StepKernels kStep_f16l_mrts;
+extern const StepKernels kStep_f16l_mrtu;
+extern const StepKernels kStep_bf16l_srt;
+extern const StepKernels kStep_bf16l_mrt;
+extern const StepKernels kStep_bf16l_mrts;
+extern const StepKernels kStep_bf16l_mrtu;
 
 const StepKernels& step_kernels(int storage, int coll) {
-    static const StepKernels* table[4][COLL_COUNT] = {
+    static const StepKernels* table[6][COLL_COUNT] = {
         {&kStep_f64_srt, &kStep_f64_mrt, &kStep_f64_mrts, &kStep_f64_mrtu},
         {&kStep_f32_srt, &kStep_f32_mrt, &kStep_f32_mrts, &kStep_f32_mrtu},
         {&kStep_f16_srt, &kStep_f16_mrt, &kStep_f16_mrts, &kStep_f16_mrtu},
         {&kStep_bf16_srt, &kStep_bf16_mrt, &kStep_bf16_mrts, &kStep_bf16_mrtu},
+        {&kStep_f16l_srt, &kStep_f16l_mrt, &kStep_f16l_mrts, &kStep_f16l_mrtu},
+        {&kStep_bf16l_srt, &kStep_bf16l_mrt, &kStep_bf16l_mrts, &kStep_bf16l_mrtu},
     };
     return *table[storage][coll];
 }

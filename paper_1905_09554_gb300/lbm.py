@@ -28,9 +28,10 @@ STATUS_NAMES = ["LBM_OK", "LBM_EINVAL", "LBM_ENOMEM", "LBM_ECUDA", "LBM_ENONFINI
 LBM_D3Q19 = 0
 LBM_SRT_SHIFT, LBM_MRT_GUO = 0, 1
 LBM_PSI_EXP = 0
-LBM_F64, LBM_F32, LBM_F16_DEV, LBM_BF16_DEV = 0, 1, 2, 3
-STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16_DEV, "bf16": LBM_BF16_DEV}
-STORAGE_BYTES = {LBM_F64: 8, LBM_F32: 4, LBM_F16_DEV: 2, LBM_BF16_DEV: 2}
+LBM_F64, LBM_F32, LBM_F16_DEV, LBM_BF16_DEV, LBM_F16_LOCAL, LBM_BF16_LOCAL = 0, 1, 2, 3, 4, 5
+STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16_DEV, "bf16": LBM_BF16_DEV,
+           "f16l": LBM_F16_LOCAL, "bf16l": LBM_BF16_LOCAL}
+STORAGE_BYTES = {LBM_F64: 8, LBM_F32: 4, LBM_F16_DEV: 2, LBM_BF16_DEV: 2, LBM_F16_LOCAL: 2, LBM_BF16_LOCAL: 2}
 COLLISION = {"srt": LBM_SRT_SHIFT, "mrt": LBM_MRT_GUO}
 
 
@@ -285,7 +286,8 @@ class Lattice:
 
     collision: 'srt' (shifted velocity) or 'mrt' (Guo forcing); rates: None
     (the paper's rule), or 19 MRT rates in moment order.  storage: 'f64',
-    'f32', 'f16' or 'bf16'.  With torch_buffers=True the two population
+    'f32', 'f16' or 'bf16' (deviations from a global rho_ref), 'f16l' or
+    'bf16l' (deviations from a per-cell reference density).  With torch_buffers=True the two population
     copies are torch.cuda tensors owned by this object and all work runs on
     torch's current stream.
     """

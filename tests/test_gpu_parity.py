@@ -172,6 +172,25 @@ def test_kernel_variant_tiling_and_chunking_do_not_change_a_bit(coll, storage):
                 assert np.array_equal(f, ref), (kernel, tile_y, zchunk)
 
 
+@pytest.mark.parametrize("coll", ["srt", "mrt"])
+def test_tensor_copy_kernel_is_bit_identical(coll):
+    """Variant 5 (one tensor-map box copy per plane) on boxes whose x size is
+    a multiple of 32 and y size a multiple of the tile height."""
+    rho = inputs.noisy_ligament_density(64, 32, 23, 6.0, 0.1, RL, RV, 1e-3, seed=21)
+    ref, _, _ = gpu_run(rho, 9, "f32", coll=coll, tau=0.8, kernel=1)
+    for tile_y in (8, 16):
+        for zchunk in (1, 4, 23):
+            f, _, _ = gpu_run(rho, 9, "f32", coll=coll, tau=0.8, kernel=5, tile_y=tile_y, zchunk=zchunk)
+            assert np.array_equal(f, ref), (tile_y, zchunk)
+
+
+def test_tensor_copy_kernel_constraints():
+    with pytest.raises(lbm.LbmError, match="LBM_EINVAL"):
+        lbm.Lattice(40, 32, 8, storage="f32", kernel=5)
+    with pytest.raises(lbm.LbmError, match="LBM_EINVAL"):
+        lbm.Lattice(64, 24, 8, storage="f32", kernel=5, tile_y=16)
+
+
 def test_bulk_kernel_on_boxes_that_wrap_inside_a_row():
     """nx = 12 < the 40-column copy window: every row copy wraps several
     times; ny = 5 and nz = 3 are smaller than a tile."""

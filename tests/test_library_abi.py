@@ -77,6 +77,24 @@ def test_create_rejects_bad_mrt_rates(lib):
     assert st == lbm.LBM_EINVAL and "rates" in lbm.lbm_last_error(None)
 
 
+def test_local_reference_storage_runs_kernel_1_only(lib):
+    for storage in (lbm.LBM_F16_LOCAL, lbm.LBM_BF16_LOCAL):
+        p = lbm.lbm_params_default()
+        p.storage = storage
+        p.kernel = 3
+        st, ctx = lbm.lbm_create(p)
+        assert st == lbm.LBM_EINVAL and not ctx.value
+        assert "kernel 1" in lbm.lbm_last_error(None)
+
+
+def test_noalloc_diagnostics_reject_local_reference_storage(lib):
+    """The local formats need a context's density field; refused before any
+    device work."""
+    st = lbm.lbm_diag_noalloc(16, lbm.LBM_F16_LOCAL, 4, 4, 8, 1.0, 1.0, 2.3, 0.1,
+                              None, None, None, None, 0, None)
+    assert st == lbm.LBM_EINVAL
+
+
 def test_null_context_calls_fail_cleanly(lib):
     assert lib.lbm_step(None, 1) == lbm.LBM_EINVAL
     assert lib.lbm_init_ligament(None, 8.0, 0.05, 1, 2.0, 2.3, 0.1) == lbm.LBM_EINVAL
