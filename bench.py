@@ -41,7 +41,8 @@ BYTES_PER_POP = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "f16l": 2, "bf16l": 2}
 # local-reference formats also read and write a float reference density per cell
 EXTRA_BYTES_PER_CELL = {"f16l": 8, "bf16l": 8}
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_NAMES = {1: "sc_step_kernel", 2: "sc_step_async_kernel", 3: "sc_step_pipe_kernel"}
+KERNEL_NAMES = {1: "sc_step_kernel", 2: "sc_step_async_kernel", 3: "sc_step_pipe_kernel", 4: "sc_step_bulk_kernel",
+                5: "sc_step_tma_kernel"}
 
 
 def parse_args():
@@ -59,7 +60,8 @@ def parse_args():
                     help="MRT rates: shear moments at 1/tau (shear) or also the energy moment (paper)")
     ap.add_argument("--zchunk", type=int, default=0)
     ap.add_argument("--tile-y", type=int, default=0)
-    ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 register-staged, 2 cp.async-staged")
+    ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 register-staged, 2 cp.async-staged, 3 pipelined, 4 bulk-copy, "
+                         "5 tensor-copy")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -70,6 +72,9 @@ def parse_args():
     ap.add_argument("--radii", default="14,28,42",
                     help="paper form: ligament radii of Tables 1-2 to run (14..98)")
     ap.add_argument("--collisions", default="srt,mrt", help="paper form: srt, mrt or both")
+    ap.add_argument("--eps", default="0.1",
+                    help="paper form: initial perturbations delta/R0 to run (Fig. 2b uses 0.1, Fig. 3 "
+                         "1/30, 0.05, 0.1)")
     ap.add_argument("--rho-ref", type=float, default=1.0,
                     help="reference density of the 16-bit deviation formats")
     ap.add_argument("--breakup-R0", type=float, default=32.0,
@@ -597,10 +602,12 @@ def run_paper(args):
     """The paper's break-up experiment (Sec. 3-4, Tables 1-2, Fig. 2b) at its
     own parameters: G0 = -5.3, Oh = 0.1, tau / rho_l / rho_v / t_cap of Table 1
     (SRT) or Table 2 (MRT, rates of Sec. 2), a box Ly x Ly x Lx with two
-    wavelengths of a 10% perturbation along the ligament (the paper's x axis
-    is this code's z axis), FP32 populations, tanh profile of width 2.  Runs
-    until the ligament breaks (min over slices of max rho below the mid
-    density) and reports T_break / t_cap beside Fig. 2b's value."""
+    wavelengths of a perturbation eps = delta/R0 along the ligament (the
+    paper's x axis is this code's z axis), FP32 populations, tanh profile of
+    width 2.  Runs until the ligament breaks (min over slices of max rho below
+    the mid density) and reports T_break / t_cap beside the paper's value
+    (Fig. 2b at eps = 0.1; Fig. 3's points at R0 = 98) and Fig. 3's linear
+    stability curve."""
     import numpy as np
     import torch
 
@@ -611,40 +618,61 @@ def run_paper(args):
     tables = {"srt": np.loadtxt(os.path.join(gold, "paper_table1_srt.txt")),
               "mrt": np.loadtxt(os.path.join(gold, "paper_table2_mrt.txt"))}
     fig = np.loadtxt(os.path.join(gold, "paper_fig2b_breakup.txt"))
+    fig3 = np.loadtxt(os.path.join(gold, "paper_fig3_points.txt"))
+    lsa = np.loadtxt(os.path.join(gold, "paper_fig3_lsa.txt"))
     radii = [int(r) for r in args.radii.split(",") if r]
+    epss = [float(e) for e in args.eps.split(",") if e]
     cases = []
-    for coll in [c for c in args.collisions.split(",") if c]:
-        for R0 in radii:
-            row = [r for r in tables[coll] if int(r[0]) == R0][0]
-            _, Lx, Ly, tau, tcap, rl, rv, sigma = row
-            nx, ny, nz = int(Ly), int(Ly), int(Lx)
-            fig_t = [f[2] for f in fig if int(f[0]) == (0 if coll == "srt" else 1) and int(f[1]) == R0][0]
-            every = max(1, int(tcap / 40))
-            with lbm.Lattice(nx, ny, nz, G=-5.3, tau=tau, collision=coll, storage="f32") as L:
-                L.init_ligament(float(R0), 0.1, rl, rv, n_waves=2)
-                ts, mins = [], []
-                t = 0
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                while t <= 20 * tcap:
-                    d = L.diag(rl, rv, raise_nonfinite=False)
+    for coll, R0, eps in [(c, r, e) for c in args.collisions.split(",") if c for r in radii for e in epss]:
+        ic = 0 if coll == "srt" else 1
+        row = [r for r in tables[coll] if int(r[0]) == R0][0]
+        _, Lx, Ly, tau, tcap, rl, rv, sigma = row
+        nx, ny, nz = int(Ly), int(Ly), int(Lx)
+        # the paper's value for this case: Fig. 2b at eps = 0.1, Fig. 3's points at R0 = 98
+        fig_t, fig_sat = None, None
+        if abs(eps - 0.1) < 1e-9:
+            fig_t, fig_sat = [(f[2], int(f[3])) for f in fig if int(f[0]) == ic and int(f[1]) == R0][0]
+        elif R0 == 98:
+            hit = [f[2] for f in fig3 if int(f[0]) == ic and abs(f[1] - eps) < 1e-6]
+            fig_t = hit[0] if hit else None
+        # linear stability analysis of the figure (kR0 = 0.687 and Oh = 0.1 at every radius)
+        lsa_t = float(np.interp(eps, lsa[:, 0], lsa[:, 1])) if lsa[0, 0] <= eps <= lsa[-1, 0] else None
+        every = max(1, int(tcap / 40))
+        with lbm.Lattice(nx, ny, nz, G=-5.3, tau=tau, collision=coll, storage="f32") as L:
+            L.init_ligament(float(R0), eps, rl, rv, n_waves=2)
+            ts, mins, drops = [], [], []
+            t, broke_at = 0, None
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            while t <= 30 * tcap:
+                d = L.diag(rl, rv, raise_nonfinite=False)
+                if d["status"] != 0:
+                    break
+                if broke_at is None:
                     ts.append(t)
                     mins.append(float(d["maxrho_z"].min()))
-                    if mins[-1] < 0.5 * (rl + rv) or d["status"] != 0:
+                    if mins[-1] < 0.5 * (rl + rv):
+                        broke_at = t
+                if broke_at is not None:
+                    # drops on the axis, for 1.5 t_cap after the pinch-off
+                    drops.append(dg.count_drops(d["maxrho_z"], rl, rv))
+                    if t >= broke_at + 1.5 * tcap:
                         break
-                    L.step(every)
-                    t += every
-                torch.cuda.synchronize()
-                wall = time.perf_counter() - t0
-                cfg = L.kernel_config()
-            tb = dg.breakup_time(ts, mins, rl, rv)
-            cases.append({"collision": coll, "R0": R0, "box": [nx, ny, nz], "tau": tau, "t_cap": tcap,
-                          "rho_l": rl, "rho_v": rv, "steps": t, "diag_every": every,
-                          "T_break_over_tcap": tb / tcap if tb is not None else None,
-                          "fig2b_T_break": fig_t,
-                          "rel_diff": (tb / tcap - fig_t) / fig_t if tb is not None else None,
-                          "wall_s": wall, "glups": nx * ny * nz * t / wall / 1e9, "kernel": cfg})
-            print(json.dumps(cases[-1]), flush=True)
+                L.step(every)
+                t += every
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            cfg = L.kernel_config()
+        tb = dg.breakup_time(ts, mins, rl, rv)
+        cases.append({"collision": coll, "R0": R0, "eps": eps, "box": [nx, ny, nz], "tau": tau, "t_cap": tcap,
+                      "rho_l": rl, "rho_v": rv, "steps": t, "diag_every": every,
+                      "drops_max": max(drops) if drops else None, "drops_final": drops[-1] if drops else None,
+                      "satellites": max(0, max(drops) - 2) if drops else None, "paper_satellites": fig_sat,
+                      "T_break_over_tcap": tb / tcap if tb is not None else None,
+                      "paper_T_break": fig_t, "lsa_T_break": lsa_t,
+                      "rel_diff": (tb / tcap - fig_t) / fig_t if tb is not None and fig_t else None,
+                      "wall_s": wall, "glups": nx * ny * nz * t / wall / 1e9, "kernel": cfg})
+        print(json.dumps(cases[-1]), flush=True)
     print(json.dumps({"metric": "paper break-up experiment (Fig. 2b) at the paper's parameters",
                       "unit": "T_break / t_cap", "data": "synthetic", "cases": cases}), flush=True)
 

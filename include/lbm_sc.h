@@ -176,6 +176,27 @@ lbm_status lbm_diag(lbm_ctx *ctx, double rho_l, double rho_v, double *mass,
 /* Select the CUDA stream (cudaStream_t) for later calls. */
 lbm_status lbm_set_stream(lbm_ctx *ctx, void *stream);
 
+/* Checkpoint / resume.  lbm_save writes the current state (the stored
+ * populations exactly as held on the device, the reference-density field of
+ * the local-reference formats, the step count t and the parameters) to
+ * `path` (written to path.tmp, then renamed, so an interrupted save leaves
+ * an existing file intact).  lbm_load restores a state saved from a context
+ * with the same box and storage (and, for the deviation formats, the same
+ * rho_ref / dev_scale): stepping on from the loaded state gives bit-identical
+ * results to never having stopped.  G, tau and the MRT rates stored in the
+ * file are informational; the context's own are used.  File layout: a
+ * 256-byte header, the populations, the reference field, a 64-bit FNV-1a
+ * checksum over 64-bit words of everything before it.  Both synchronise the
+ * context's stream; both stage through 2 x 32 MiB of pinned host memory
+ * allocated for the call.
+ * Returns LBM_EIO if the file cannot be opened, written or read, is
+ * truncated, has trailing bytes or fails the checksum (the context's state is
+ * then unchanged: the file is read into the spare copy and made current only
+ * after the checksum matches), LBM_EINVAL for a box/storage mismatch, a
+ * batch box, or an empty path. */
+lbm_status lbm_save(lbm_ctx *ctx, const char *path);
+lbm_status lbm_load(lbm_ctx *ctx, const char *path);
+
 /* Bytes of device memory the context allocated itself. */
 long long lbm_device_bytes(const lbm_ctx *ctx);
 

@@ -1415,4 +1415,230 @@ lbm_status lbm_adjoint_backward(lbm_ctx* c, const double* dJdrho, int in_on_devi
     return LBM_OK;
 }
 
+// ----------------------------------------------------------------------------
+// Checkpoint / resume (lbm_save, lbm_load)
+// ----------------------------------------------------------------------------
+// File layout (little-endian, as both supported hosts are): a 256-byte header
+// (CkptHeader, zero padded), the stored populations of the current copy
+// exactly as the device holds them (19 * n elements of the storage type), the
+// float reference-density field for the local-reference formats, then a
+// 64-bit checksum of everything before it: FNV-1a over 64-bit little-endian
+// words (the offset basis and prime of 64-bit FNV-1a), the byte tail folded
+// in one byte at a time.
+struct CkptHeader {
+    char magic[8];         // "LBMSCKP\0"
+    uint32_t version;      // 1
+    uint32_t header_bytes; // 256
+    int32_t nx, ny, nz, storage, collision, pad0;
+    int64_t t;
+    double G, tau, rho0, rho_ref, dev_scale;
+    double s[Q];
+    uint64_t pop_bytes, ref_bytes;
+};
+static_assert(sizeof(CkptHeader) <= 256, "checkpoint header must fit in 256 bytes");
+
+struct Fnv64 {
+    uint64_t h = 0xcbf29ce484222325ULL;
+    unsigned char tail[8];
+    int ntail = 0;
+    void word(uint64_t w) { h = (h ^ w) * 0x100000001b3ULL; }
+    void add(const void* p, size_t len) {
+        const unsigned char* b = static_cast<const unsigned char*>(p);
+        while (len && ntail) {  // complete a pending word first
+            tail[ntail++] = *b++;
+            --len;
+            if (ntail == 8) {
+                uint64_t w;
+                memcpy(&w, tail, 8);
+                word(w);
+                ntail = 0;
+            }
+        }
+        for (; len >= 8; len -= 8, b += 8) {
+            uint64_t w;
+            memcpy(&w, b, 8);
+            word(w);
+        }
+        while (len--) tail[ntail++] = *b++;
+    }
+    uint64_t finish() {
+        for (int k = 0; k < ntail; ++k) h = (h ^ tail[k]) * 0x100000001b3ULL;
+        ntail = 0;
+        return h;
+    }
+};
+
+static const size_t kCkptChunk = size_t(32) << 20;  // bytes per host staging buffer
+
+// Device -> file through two pinned staging buffers (the copy of one chunk
+// overlaps the write of the previous one).
+static lbm_status ckpt_write_device(lbm_ctx* c, FILE* fp, const void* dev, size_t bytes, Fnv64& fnv,
+                                    unsigned char* const (&buf)[2], cudaEvent_t const (&ev)[2]) {
+    const char* src = static_cast<const char*>(dev);
+    size_t issued = 0, written = 0;
+    size_t len[2] = {0, 0};
+    int k = 0;
+    auto issue = [&](int slot) -> cudaError_t {
+        len[slot] = bytes - issued < kCkptChunk ? bytes - issued : kCkptChunk;
+        cudaError_t e = cudaMemcpyAsync(buf[slot], src + issued, len[slot], cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[slot], c->stream);
+        issued += len[slot];
+        return e;
+    };
+    if (bytes) LBM_CUDA(c, issue(0));
+    while (written < bytes) {
+        if (issued < bytes) LBM_CUDA(c, issue(k ^ 1));
+        LBM_CUDA(c, cudaEventSynchronize(ev[k]));
+        fnv.add(buf[k], len[k]);
+        if (fwrite(buf[k], 1, len[k], fp) != len[k]) return c->fail(LBM_EIO, "lbm_save: write failed");
+        written += len[k];
+        k ^= 1;
+    }
+    return LBM_OK;
+}
+
+// File -> device (into `dev`) through the pinned staging buffers.
+static lbm_status ckpt_read_device(lbm_ctx* c, FILE* fp, void* dev, size_t bytes, Fnv64& fnv,
+                                   unsigned char* const (&buf)[2], cudaEvent_t const (&ev)[2], const char* path) {
+    char* dst = static_cast<char*>(dev);
+    size_t done = 0;
+    bool used[2] = {false, false};
+    int k = 0;
+    while (done < bytes) {
+        const size_t len = bytes - done < kCkptChunk ? bytes - done : kCkptChunk;
+        if (used[k]) LBM_CUDA(c, cudaEventSynchronize(ev[k]));  // the copy out of buf[k] has finished
+        if (fread(buf[k], 1, len, fp) != len) return c->fail(LBM_EIO, "lbm_load: %s is truncated", path);
+        fnv.add(buf[k], len);
+        LBM_CUDA(c, cudaMemcpyAsync(dst + done, buf[k], len, cudaMemcpyHostToDevice, c->stream));
+        LBM_CUDA(c, cudaEventRecord(ev[k], c->stream));
+        used[k] = true;
+        done += len;
+        k ^= 1;
+    }
+    return LBM_OK;
+}
+
+// Pinned staging buffers and their events for one save or load.
+struct CkptStaging {
+    unsigned char* buf[2] = {nullptr, nullptr};
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    ~CkptStaging() {
+        for (int k = 0; k < 2; ++k) {
+            if (ev[k]) cudaEventSynchronize(ev[k]);
+            if (buf[k]) cudaFreeHost(buf[k]);
+            if (ev[k]) cudaEventDestroy(ev[k]);
+        }
+    }
+    cudaError_t init() {
+        for (int k = 0; k < 2; ++k) {
+            cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&buf[k]), kCkptChunk);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+};
+
+static void ckpt_fill_header(const lbm_ctx* c, CkptHeader& h) {
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, "LBMSCKP", 8);
+    h.version = 1;
+    h.header_bytes = 256;
+    h.nx = c->p.nx;
+    h.ny = c->p.ny;
+    h.nz = c->p.nz;
+    h.storage = c->p.storage;
+    h.collision = c->p.collision;
+    h.t = c->t;
+    h.G = c->p.G;
+    h.tau = c->p.tau;
+    h.rho0 = c->p.rho0;
+    h.rho_ref = c->p.rho_ref;
+    h.dev_scale = c->p.dev_scale;
+    for (int k = 0; k < Q; ++k) h.s[k] = c->args.s[k];
+    h.pop_bytes = (uint64_t)Q * (uint64_t)c->n * c->elem;
+    h.ref_bytes = c->ref[0] ? sizeof(float) * (uint64_t)c->n : 0;
+}
+
+lbm_status lbm_save(lbm_ctx* c, const char* path) {
+    if (!c) return LBM_EINVAL;
+    if (!path || !path[0]) return c->fail(LBM_EINVAL, "lbm_save: empty path");
+    if (c->batch) return c->fail(LBM_EINVAL, "lbm_save: this context is a box of a batch");
+    if (lbm_status st = check_device_error(c); st != LBM_OK) return st;
+    CkptStaging stg;
+    LBM_CUDA(c, stg.init());
+    unsigned char head[256] = {0};
+    CkptHeader h;
+    ckpt_fill_header(c, h);
+    memcpy(head, &h, sizeof(h));
+    // write to path.tmp and rename over path once complete, so an interrupted
+    // save never replaces a good checkpoint with a partial one
+    std::vector<char> tmp(strlen(path) + 5);
+    snprintf(tmp.data(), tmp.size(), "%s.tmp", path);
+    FILE* fp = fopen(tmp.data(), "wb");
+    if (!fp) return c->fail(LBM_EIO, "lbm_save: cannot open %s for writing", tmp.data());
+    Fnv64 fnv;
+    fnv.add(head, sizeof(head));
+    lbm_status st = fwrite(head, 1, sizeof(head), fp) == sizeof(head)
+                        ? LBM_OK
+                        : c->fail(LBM_EIO, "lbm_save: write failed");
+    if (st == LBM_OK) st = ckpt_write_device(c, fp, c->f[c->cur], h.pop_bytes, fnv, stg.buf, stg.ev);
+    if (st == LBM_OK && h.ref_bytes) st = ckpt_write_device(c, fp, c->ref[c->cur], h.ref_bytes, fnv, stg.buf, stg.ev);
+    if (st == LBM_OK) {
+        const uint64_t sum = fnv.finish();
+        if (fwrite(&sum, 1, 8, fp) != 8) st = c->fail(LBM_EIO, "lbm_save: write failed");
+    }
+    if (fclose(fp) != 0 && st == LBM_OK) st = c->fail(LBM_EIO, "lbm_save: close failed");
+    if (st == LBM_OK && rename(tmp.data(), path) != 0) st = c->fail(LBM_EIO, "lbm_save: cannot rename to %s", path);
+    if (st != LBM_OK) remove(tmp.data());
+    return st;
+}
+
+lbm_status lbm_load(lbm_ctx* c, const char* path) {
+    if (!c) return LBM_EINVAL;
+    if (!path || !path[0]) return c->fail(LBM_EINVAL, "lbm_load: empty path");
+    if (c->batch) return c->fail(LBM_EINVAL, "lbm_load: this context is a box of a batch");
+    if (lbm_status st = check_device_error(c); st != LBM_OK) return st;
+    FILE* fp = fopen(path, "rb");
+    if (!fp) return c->fail(LBM_EIO, "lbm_load: cannot open %s", path);
+    struct Closer {
+        FILE* f;
+        ~Closer() { fclose(f); }
+    } closer{fp};
+    unsigned char head[256];
+    if (fread(head, 1, sizeof(head), fp) != sizeof(head)) return c->fail(LBM_EIO, "lbm_load: %s is truncated", path);
+    CkptHeader h;
+    memcpy(&h, head, sizeof(h));
+    if (memcmp(h.magic, "LBMSCKP", 8) != 0 || h.version != 1 || h.header_bytes != 256)
+        return c->fail(LBM_EIO, "lbm_load: %s is not a version-1 checkpoint", path);
+    CkptHeader mine;
+    ckpt_fill_header(c, mine);
+    if (h.nx != mine.nx || h.ny != mine.ny || h.nz != mine.nz || h.storage != mine.storage)
+        return c->fail(LBM_EINVAL, "lbm_load: %s holds a %dx%dx%d box with storage %d; the context is %dx%dx%d, %d",
+                       path, h.nx, h.ny, h.nz, h.storage, mine.nx, mine.ny, mine.nz, mine.storage);
+    if (h.storage >= LBM_F16_DEV && (h.dev_scale != mine.dev_scale ||
+                                     (h.storage < LBM_F16_LOCAL && h.rho_ref != mine.rho_ref)))
+        return c->fail(LBM_EINVAL, "lbm_load: %s was written with another rho_ref / dev_scale", path);
+    if (h.pop_bytes != mine.pop_bytes || h.ref_bytes != mine.ref_bytes || h.t < 0)
+        return c->fail(LBM_EIO, "lbm_load: %s has an inconsistent header", path);
+    CkptStaging stg;
+    LBM_CUDA(c, stg.init());
+    // read into the other copy (the next step overwrites it anyway) and make
+    // it current only once the checksum matches
+    const int nxt = c->cur ^ 1;
+    Fnv64 fnv;
+    fnv.add(head, sizeof(head));
+    lbm_status st = ckpt_read_device(c, fp, c->f[nxt], h.pop_bytes, fnv, stg.buf, stg.ev, path);
+    if (st == LBM_OK && h.ref_bytes) st = ckpt_read_device(c, fp, c->ref[nxt], h.ref_bytes, fnv, stg.buf, stg.ev, path);
+    if (st != LBM_OK) return st;
+    uint64_t sum = 0;
+    if (fread(&sum, 1, 8, fp) != 8) return c->fail(LBM_EIO, "lbm_load: %s is truncated", path);
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (sum != fnv.finish()) return c->fail(LBM_EIO, "lbm_load: checksum mismatch in %s", path);
+    if (fgetc(fp) != EOF) return c->fail(LBM_EIO, "lbm_load: trailing bytes in %s", path);
+    c->cur = nxt;
+    c->t = (long)h.t;
+    return LBM_OK;
+}
+
 }  // extern "C"

@@ -9,7 +9,11 @@ growth).  Pure numpy; no lattice arithmetic.
   two samples that bracket it;
 * growth rate: least-squares slope of ln|a_k(t)|, a_k the cos(2 pi z / nz)
   coefficient of R(z, t), over a window [t_start, first t with
-  |a_k| >= a_stop).
+  |a_k| >= a_stop);
+* drops after break-up: the maximal runs (periodic in z) of slices that hold
+  liquid (max rho above the mid density); with the drops on the ligament's
+  axis each run is one drop, and drops beyond the number of perturbation
+  wavelengths are satellites (Fig. 2b's filled symbols).
 """
 
 from __future__ import annotations
@@ -61,3 +65,16 @@ def growth_rate(times, amplitudes, t_start: float, a_stop: float, min_points: in
     if sel.sum() < min_points:
         return None
     return float(np.polyfit(t[sel], np.log(a[sel]), 1)[0])
+
+
+def count_drops(maxrho_z, rho_l, rho_v):
+    """Number of maximal periodic runs of z slices whose max rho exceeds
+    (rho_l + rho_v)/2; 0 if no slice holds liquid, 1 if every slice does
+    (an unbroken ligament)."""
+    liquid = np.asarray(maxrho_z, dtype=float) > 0.5 * (rho_l + rho_v)
+    if not liquid.any():
+        return 0
+    if liquid.all():
+        return 1
+    # a run starts where a liquid slice follows a dry one (wrapping around z)
+    return int(np.count_nonzero(liquid & ~np.roll(liquid, 1)))

@@ -76,6 +76,8 @@ _SIGNATURES = {
     "lbm_moments": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int]),
     "lbm_diag": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _D, _D, _D, _D]),
     "lbm_set_stream": (ctypes.c_int, [_P, _P]),
+    "lbm_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "lbm_load": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "lbm_device_bytes": (ctypes.c_longlong, [_P]),
     "lbm_params_sizeof": (ctypes.c_longlong, []),
     "lbm_kernel_config": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -195,6 +197,14 @@ def lbm_diag(ctx, rho_l, rho_v, mass, mom, area_z, maxrho_z):
 
 def lbm_set_stream(ctx, stream):
     return load().lbm_set_stream(ctx, stream)
+
+
+def lbm_save(ctx, path):
+    return load().lbm_save(ctx, os.fsencode(path))
+
+
+def lbm_load(ctx, path):
+    return load().lbm_load(ctx, os.fsencode(path))
 
 
 def lbm_device_bytes(ctx):
@@ -450,6 +460,14 @@ class Lattice:
             res, op, odev = out, out.data_ptr(), 1
         self._check(lbm_adjoint_backward(self.ctx, gp, gdev, op, odev, ctypes.byref(dG), ctypes.byref(dT)))
         return res, dG.value, dT.value
+
+    def save(self, path):
+        """Checkpoint the current state to `path` (lbm_save)."""
+        self._check(lbm_save(self.ctx, path))
+
+    def load(self, path):
+        """Restore a state written by save() (lbm_load)."""
+        self._check(lbm_load(self.ctx, path))
 
     def kernel_config(self):
         st, cfg = lbm_kernel_config(self.ctx)

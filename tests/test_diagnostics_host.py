@@ -38,3 +38,16 @@ def test_growth_rate_recovers_an_exponential_and_stops_at_threshold():
     a[t > 250] = 5.0  # beyond the stop amplitude: must be excluded
     assert abs(dg.growth_rate(t, a, t_start=50, a_stop=1.0) - 0.02) < 1e-12
     assert dg.growth_rate(t[:3], a[:3], t_start=0, a_stop=1.0) is None
+
+
+def test_count_drops_counts_periodic_liquid_runs():
+    rl, rv = 2.2, 0.1
+    L, V = 2.0, 0.2  # liquid / vapour slice maxima
+    assert dg.count_drops([L] * 8, rl, rv) == 1  # unbroken ligament
+    assert dg.count_drops([V] * 8, rl, rv) == 0
+    # two main drops and one satellite between them
+    assert dg.count_drops([L, L, V, L, V, L, L, V], rl, rv) == 3
+    # a run that wraps around z is one drop
+    assert dg.count_drops([L, V, V, L, L, V, L, L], rl, rv) == 2
+    # the mid density itself is not liquid
+    assert dg.count_drops([1.15, V, L, V], rl, rv) == 1

@@ -1,0 +1,108 @@
+"""Checkpoint / resume (lbm_save, lbm_load).
+
+* Resume is exact: save at step k, run on, load, run on again: the state
+  after the second run is bit-identical to the first and to an uninterrupted
+  run, for every storage format (the file holds the stored bits).
+* A damaged file (flipped byte, truncation, trailing bytes, foreign file) is
+  refused with LBM_EIO and leaves the context's state untouched; a file of
+  another box or storage is refused with LBM_EINVAL.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+from paper_1905_09554_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - GPU machine only
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1905_09554_gb300 import lbm  # noqa: E402
+
+RL, RV = inputs.COEXISTENCE[("shift", -5.5, 1.0)]
+SHAPE = (32, 24, 40)
+
+
+def make(storage="f32", **kw):
+    L = lbm.Lattice(*SHAPE, G=-5.5, tau=1.0, storage=storage, **kw)
+    L.init_ligament(6.0, 0.1, RL, RV)
+    return L
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16l"])
+def test_resume_is_bit_identical(tmp_path, storage):
+    path = str(tmp_path / "state.ckpt")
+    with make(storage) as L:
+        L.step(7)
+        L.save(path)
+        L.step(11)
+        first = L.get_populations()
+        t_first = L.time()
+        L.load(path)
+        assert L.time() == 7
+        L.step(11)
+        again = L.get_populations()
+        assert L.time() == t_first == 18
+    assert np.array_equal(first, again)
+    with make(storage) as M:  # a fresh context resumes the same run
+        M.load(path)
+        M.step(11)
+        assert np.array_equal(M.get_populations(), first)
+    with make(storage) as N:  # and the uninterrupted run agrees
+        N.step(18)
+        assert np.array_equal(N.get_populations(), first)
+
+
+def test_damaged_files_are_refused_and_state_kept(tmp_path):
+    path = str(tmp_path / "state.ckpt")
+    with make() as L:
+        L.step(5)
+        L.save(path)
+        L.step(3)
+        before = L.get_populations()
+        good = open(path, "rb").read()
+        cases = {
+            "flip": good[:1000] + bytes([good[1000] ^ 0x10]) + good[1001:],
+            "truncated": good[:-9],
+            "trailing": good + b"\0",
+            "foreign": b"not a checkpoint" * 32,
+        }
+        for name, data in cases.items():
+            bad = str(tmp_path / f"{name}.ckpt")
+            with open(bad, "wb") as fh:
+                fh.write(data)
+            st = lbm.lbm_load(L.ctx, bad)
+            assert st == lbm.LBM_EIO, name
+            assert L.time() == 8
+            assert np.array_equal(L.get_populations(), before), name
+        assert lbm.lbm_load(L.ctx, str(tmp_path / "missing.ckpt")) == lbm.LBM_EIO
+        L.load(path)  # the good file still loads
+        assert L.time() == 5
+
+
+def test_mismatched_box_or_storage_is_refused(tmp_path):
+    path = str(tmp_path / "state.ckpt")
+    with make() as L:
+        L.save(path)
+    with lbm.Lattice(32, 24, 41, G=-5.5) as M:
+        assert lbm.lbm_load(M.ctx, path) == lbm.LBM_EINVAL
+        assert "box" in lbm.lbm_last_error(M.ctx)
+    with lbm.Lattice(*SHAPE, G=-5.5, storage="f16") as M:
+        assert lbm.lbm_load(M.ctx, path) == lbm.LBM_EINVAL
+
+
+def test_save_replaces_atomically(tmp_path):
+    """A save leaves no temporary file behind and overwrites the old file."""
+    path = str(tmp_path / "state.ckpt")
+    with make() as L:
+        L.save(path)
+        L.step(2)
+        L.save(path)
+        L.step(2)
+        L.load(path)
+        assert L.time() == 2
+    assert os.listdir(tmp_path) == ["state.ckpt"]

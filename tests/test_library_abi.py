@@ -96,6 +96,8 @@ def test_noalloc_diagnostics_reject_local_reference_storage(lib):
 
 
 def test_null_context_calls_fail_cleanly(lib):
+    assert lbm.lbm_save(None, "x.ckpt") == lbm.LBM_EINVAL
+    assert lbm.lbm_load(None, "x.ckpt") == lbm.LBM_EINVAL
     assert lib.lbm_step(None, 1) == lbm.LBM_EINVAL
     assert lib.lbm_init_ligament(None, 8.0, 0.05, 1, 2.0, 2.3, 0.1) == lbm.LBM_EINVAL
     assert lib.lbm_time(None) == -1
