@@ -308,8 +308,11 @@ StepLaunch step_launch(const lbm_ctx* c) {
 }
 
 int prepare_async(lbm_ctx* c) {
-    if (c->p.storage != LBM_F64 && c->p.storage != LBM_F32) return 0;
-    return step_kernels(c->p.storage, c->coll).prepare(step_launch(c));
+    const int st = c->p.storage;
+    // 16-bit global-reference storage: the pipelined kernel only, with nx even
+    const bool word16 = (st == LBM_F16_DEV || st == LBM_BF16_DEV) && c->kernel == 3 && c->p.nx % 2 == 0;
+    if (st != LBM_F64 && st != LBM_F32 && !word16) return 0;
+    return step_kernels(st, c->coll).prepare(step_launch(c));
 }
 
 cudaError_t launch_step(const lbm_ctx* c, const void* src, void* dst) {
@@ -639,8 +642,8 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
                          p->kernel, cudaGetErrorString(cudaError_t(-per_sm)));
             else
                 snprintf(g_create_err, sizeof(g_create_err),
-                         "lbm_create: kernel %d needs FP64/FP32 storage (kernel 2 with FP64: tile_y <= 8) "
-                         "and must fit on an SM",
+                         "lbm_create: kernel %d needs FP64/FP32 storage (kernel 2 with FP64: tile_y <= 8; "
+                         "kernel 3 also takes FP16/BF16 deviations with nx even) and must fit on an SM",
                          p->kernel);
             lbm_destroy(c);
             return LBM_EINVAL;

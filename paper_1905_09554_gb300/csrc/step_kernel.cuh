@@ -22,6 +22,7 @@
 #include <cuda.h>
 
 #include <cstdint>
+#include <cstring>
 
 #include "codec.cuh"
 #include "lattice.cuh"
@@ -630,7 +631,8 @@ sc_step_async_kernel(const typename Codec::S* __restrict__ src, typename Codec::
 }
 
 // ----------------------------------------------------------------------------
-// Pipelined variant (FP32 / FP64 storage).
+// Pipelined variant (FP32 / FP64 storage, and the global-reference 16-bit
+// formats with nx even).
 //
 // The register-staged kernel waits for each plane's loads right after issuing
 // them.  Here the loads of plane z+2 are issued before the collision of
@@ -639,20 +641,37 @@ sc_step_async_kernel(const typename Codec::S* __restrict__ src, typename Codec::
 // only for psi) go through a three-stage cp.async buffer two planes ahead,
 // so ring loads never stall the block's barrier.  Persistent grid over
 // (xy tile, z chunk) work items as in sc_step_async_kernel.
+//
+// 16-bit storage: cp.async moves at least 4 bytes, so each ring cell copies
+// the aligned 4-byte word that holds it (with nx even a row never splits a
+// word: the cell at even x is the low half, at odd x the high half), and the
+// prefetched plane is kept as raw 16-bit values, decoded after the collision
+// so that the decode does not wait for the loads.
 // ----------------------------------------------------------------------------
 template <class Codec, int TX, int TY>
 struct PipeLayout {
     using S = typename Codec::S;
     using R = typename Codec::R;
+    static constexpr bool kWord = sizeof(S) == 2;  // ring cells as aligned 4-byte words
+    using HS = std::conditional_t<kWord, uint32_t, S>;
     static constexpr int NT = TX * TY;
     static constexpr int NHALO = 2 * (TX + 2) + 2 * TY;
     static constexpr int PX = TX + 2;
     static constexpr int PLANE = PX * (TY + 2);
     static constexpr int NSTAGE = 3;
     static constexpr int NSLOT = 4;
-    static constexpr size_t stage_bytes = sizeof(S) * Q * NHALO;
+    static constexpr size_t stage_bytes = sizeof(HS) * Q * NHALO;
     static constexpr size_t bytes = NSTAGE * stage_bytes + sizeof(R) * NSLOT * PLANE;
 };
+
+// The 16-bit value in the low (hi = 0) or high (hi = 1) half of a word.
+template <class S>
+__device__ __forceinline__ S half_of(uint32_t w, int hi) {
+    const unsigned short b = hi ? (unsigned short)(w >> 16) : (unsigned short)(w & 0xffffu);
+    S v;
+    memcpy(&v, &b, sizeof(b));
+    return v;
+}
 
 // Register budget: at most 65536 / (512 threads) = 128 registers per thread
 // so that 512 threads per SM stay resident.  I is the element-offset type:
@@ -671,10 +690,12 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src_all, typename Code
     using R = typename Codec::R;
     using S = typename Codec::S;
     using L = PipeLayout<Codec, TX, TY>;
+    using HS = typename L::HS;
     constexpr int PX = L::PX, PLANE = L::PLANE, NH = L::NHALO;
     static_assert(L::NHALO <= TX * TY, "tile too small for its halo ring");
+    static_assert(!Codec::kLocal, "local-reference storage runs the register-staged kernel");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    S* hstage = reinterpret_cast<S*>(smem_raw);  // [NSTAGE][Q][NHALO]
+    HS* hstage = reinterpret_cast<HS*>(smem_raw);  // [NSTAGE][Q][NHALO]
     R* ring = reinterpret_cast<R*>(smem_raw + L::NSTAGE * L::stage_bytes);
 
     const int tid = threadIdx.x;
@@ -735,6 +756,7 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src_all, typename Code
         const bool active = (x0 + lx < nx) && (y0 + ly < ny);
         const I my_xy = I(gy) * I(nx) + I(gx);
         const I h_xy = (h_slot >= 0) ? I(wrap_index(y0 + hy, ny)) * I(nx) + I(wrap_index(x0 + hx, nx)) : I(0);
+        const int hpar = L::kWord ? int(h_xy & 1) : 0;  // 16-bit: half of the ring cell's word
         const int xp = (gx + 1 == nx) ? 0 : gx + 1, xm = (gx == 0) ? nx - 1 : gx - 1;
         const int yp = (gy + 1 == ny) ? 0 : gy + 1, ym = (gy == 0) ? ny - 1 : gy - 1;
         const I yoff[3] = {I(ym) * I(nx), I(gy) * I(nx), I(yp) * I(nx)};
@@ -745,22 +767,23 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src_all, typename Code
         auto slot_of = [&](int z) { return (z - zs + 1) & (L::NSLOT - 1); };
         auto issue_halo = [&](int z) {
             if (h_slot >= 0) {
-                const S* base = src + (I(wrapz(z)) * plane + h_xy);
-                S* st = hstage + stage_of(z) * (Q * NH);
+                const S* base = src + (I(wrapz(z)) * plane + h_xy - hpar);
+                HS* st = hstage + stage_of(z) * (Q * NH);
                 static_for<0, Q>([&](auto qc) {
                     constexpr int q = decltype(qc)::value;
-                    async_copy::copy<sizeof(S)>(st + q * NH + h, base + I(q) * n);
+                    async_copy::copy<sizeof(HS)>(st + q * NH + h, base + I(q) * n);
                 });
             }
             async_copy::commit();
         };
         auto halo_psi = [&](int z) {
             if (h_slot >= 0) {
-                const S* st = hstage + stage_of(z) * (Q * NH);
+                const HS* st = hstage + stage_of(z) * (Q * NH);
                 R r = R(0);
                 static_for<0, Q>([&](auto qc) {
                     constexpr int q = decltype(qc)::value;
-                    r += Codec::template decode<q>(st[q * NH + h], dev);
+                    if constexpr (L::kWord) r += Codec::template decode<q>(half_of<S>(st[q * NH + h], hpar), dev);
+                    else r += Codec::template decode<q>(st[q * NH + h], dev);
                 });
                 ring[slot_of(z) * PLANE + h_slot] = psi_of<R>(r, rho0, inv_rho0);
             }
@@ -807,22 +830,75 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src_all, typename Code
         issue_halo(zs - 1);
         issue_halo(zs);
         issue_halo(zs + 1);
-        R fa[Q], fb[Q], fcc[Q];
-        load_plane(fa, zs - 1);
-        own_psi(fa, zs - 1);
-        load_plane(fa, zs);
-        load_plane(fb, zs + 1);
-        async_copy::wait<2>();
-        halo_psi(zs - 1);
-        async_copy::wait<1>();
-        halo_psi(zs);
-        own_psi(fa, zs);
-        own_psi(fb, zs + 1);
+        if constexpr (L::kWord) {
+            // fc holds plane z (decoded), the other array plane z+1; the raw
+            // loads of z+2 land in fr and are decoded into fc once plane z is
+            // stored.  Two arrays alternate.
+            S fr[Q];
+            auto body16 = [&](R (&fc)[Q], int z) {
+                const bool more = z + 2 <= ze;
+                if (more) {
+                    const S* base = src + (I(wrapz(z + 2)) * plane + my_xy);
+                    static_for<0, Q>([&](auto qc) {
+                        constexpr int q = decltype(qc)::value;
+                        fr[q] = __ldg(base + I(q) * n);
+                    });
+                    issue_halo(z + 2);
+                } else {
+                    async_copy::commit();
+                }
+                async_copy::wait<1>();
+                halo_psi(z + 1);
+                __syncthreads();
+                if (active) {
+                    const int zm = (z == 0) ? nz - 1 : z - 1;
+                    const int zn = (z + 1 == nz) ? 0 : z + 1;
+                    const I zoff[3] = {I(zm) * plane, I(z) * plane, I(zn) * plane};
+                    update_cell<Codec, COLL, PX, I>(fc, ring + slot_of(z - 1) * PLANE, ring + slot_of(z) * PLANE,
+                                                    ring + slot_of(z + 1) * PLANE, my_slot, dst, n, zoff, yoff,
+                                                    xidx, a);
+                }
+                if (more) {
+                    static_for<0, Q>([&](auto qc) {
+                        constexpr int q = decltype(qc)::value;
+                        fc[q] = Codec::template decode<q>(fr[q], dev);
+                    });
+                    own_psi(fc, z + 2);
+                }
+            };
+            R fa[Q], fb[Q];
+            load_plane(fa, zs - 1);
+            own_psi(fa, zs - 1);
+            load_plane(fa, zs);
+            load_plane(fb, zs + 1);
+            async_copy::wait<2>();
+            halo_psi(zs - 1);
+            async_copy::wait<1>();
+            halo_psi(zs);
+            own_psi(fa, zs);
+            own_psi(fb, zs + 1);
+            for (int z = zs; z < ze; z += 2) {
+                body16(fa, z);
+                if (z + 1 < ze) body16(fb, z + 1);
+            }
+        } else {
+            R fa[Q], fb[Q], fcc[Q];
+            load_plane(fa, zs - 1);
+            own_psi(fa, zs - 1);
+            load_plane(fa, zs);
+            load_plane(fb, zs + 1);
+            async_copy::wait<2>();
+            halo_psi(zs - 1);
+            async_copy::wait<1>();
+            halo_psi(zs);
+            own_psi(fa, zs);
+            own_psi(fb, zs + 1);
 
-        for (int z = zs; z < ze; z += 3) {
-            body(fa, fb, fcc, z);
-            if (z + 1 < ze) body(fb, fcc, fa, z + 1);
-            if (z + 2 < ze) body(fcc, fa, fb, z + 2);
+            for (int z = zs; z < ze; z += 3) {
+                body(fa, fb, fcc, z);
+                if (z + 1 < ze) body(fb, fcc, fa, z + 1);
+                if (z + 2 < ze) body(fcc, fa, fb, z + 2);
+            }
         }
     }
     async_copy::wait<0>();

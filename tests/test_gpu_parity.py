@@ -224,10 +224,29 @@ def test_bulk_kernel_needs_fp32_and_nx_multiple_of_4():
         lbm.Lattice(8, 8, 8, storage="f64", kernel=4)
 
 
-@pytest.mark.parametrize("kernel", [2, 3])
-def test_staged_kernels_reject_16_bit_storage(kernel):
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("coll", ["srt", "mrt"])
+def test_pipelined_kernel_with_16_bit_storage_is_bit_identical(coll, storage):
+    """The pipelined kernel's 16-bit path (ring cells copied as the aligned
+    4-byte word that holds them, raw prefetch decoded after the collision)
+    against the register-staged kernel; nx = 34 gives a partial second tile
+    whose ring wraps to x = 0."""
+    for shape in ((40, 12, 23), (34, 10, 9)):
+        rho = inputs.noisy_ligament_density(*shape, 3.0, 0.1, RL, RV, 1e-3, seed=5)
+        ref, _, _ = gpu_run(rho, 10, storage, coll=coll, tau=0.8, kernel=1)
+        for tile_y in (4, 8, 16):
+            for zchunk in (1, 5, 23):
+                f, _, _ = gpu_run(rho, 10, storage, coll=coll, tau=0.8, kernel=3, tile_y=tile_y, zchunk=zchunk)
+                assert np.array_equal(f, ref), (shape, tile_y, zchunk)
+
+
+def test_staged_kernels_reject_unsupported_16_bit_layouts():
     with pytest.raises(lbm.LbmError, match="LBM_EINVAL"):
-        lbm.Lattice(8, 8, 8, storage="f16", kernel=kernel)
+        lbm.Lattice(8, 8, 8, storage="f16", kernel=2)
+    with pytest.raises(lbm.LbmError, match="LBM_EINVAL"):
+        lbm.Lattice(9, 8, 8, storage="f16", kernel=3)  # nx odd
+    with pytest.raises(lbm.LbmError, match="LBM_EINVAL"):
+        lbm.Lattice(8, 8, 8, storage="f16l", kernel=3)
 
 
 @pytest.mark.parametrize("shape", [(1, 1, 32), (1, 1, 1), (5, 1, 1), (1, 7, 3), (2, 3, 2), (33, 1, 2)])
