@@ -82,8 +82,8 @@ typedef struct {
                              initialised, and by every step to the density of the
                              cell before the step (so f(t+1) is stored relative to
                              rho(t), which differs from rho(t+1) by O(|div j|)).
-                             Local-reference storage runs step kernel 1 only and is
-                             not accepted by batches, the adjoint or
+                             Local-reference storage runs step kernel 1 or 3 and
+                             is not accepted by batches, the adjoint or
                              lbm_diag_noalloc.                                        */
     double dev_scale;     /* deviation storage scale (> 0)                          */
     void *stream;         /* cudaStream_t for all work; NULL = legacy default       */
@@ -95,7 +95,8 @@ typedef struct {
     int tile_y;           /* step kernel: tile height (4, 8 or 16); 0 = auto        */
     int kernel;           /* step kernel variant: 0 = auto, 1 = register-staged,
                              2 = cp.async-staged persistent, 3 = pipelined
-                             persistent (2 and 3: FP64/FP32 storage only),
+                             persistent (2: FP64/FP32 storage; 3: also the
+                             16-bit formats when nx is even),
                              4 = warp-specialised bulk-copy (FP32, nx % 4 == 0),
                              5 = tensor-copy pipeline (FP32, tile_y 8 or 16,
                              nx % 32 == 0, ny % tile_y == 0; steps on buffers

@@ -309,8 +309,8 @@ StepLaunch step_launch(const lbm_ctx* c) {
 
 int prepare_async(lbm_ctx* c) {
     const int st = c->p.storage;
-    // 16-bit global-reference storage: the pipelined kernel only, with nx even
-    const bool word16 = (st == LBM_F16_DEV || st == LBM_BF16_DEV) && c->kernel == 3 && c->p.nx % 2 == 0;
+    // 16-bit storage: the pipelined kernel only, with nx even
+    const bool word16 = st >= LBM_F16_DEV && c->kernel == 3 && c->p.nx % 2 == 0;
     if (st != LBM_F64 && st != LBM_F32 && !word16) return 0;
     return step_kernels(st, c->coll).prepare(step_launch(c));
 }
@@ -489,8 +489,8 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     if (p->storage < LBM_F64 || p->storage > LBM_BF16_LOCAL) return create_fail(LBM_EINVAL, "lbm_create: unknown storage");
     if (p->storage >= LBM_F16_DEV && (!(p->dev_scale > 0) || !std::isfinite(p->rho_ref)))
         return create_fail(LBM_EINVAL, "lbm_create: deviation storage needs dev_scale > 0 and finite rho_ref");
-    if (p->storage >= LBM_F16_LOCAL && p->kernel > 1)
-        return create_fail(LBM_EINVAL, "lbm_create: local-reference storage runs kernel 1 only");
+    if (p->storage >= LBM_F16_LOCAL && (p->kernel == 2 || p->kernel >= 4))
+        return create_fail(LBM_EINVAL, "lbm_create: local-reference storage runs kernel 1 or 3");
     if (p->collision == LBM_MRT_GUO && p->has_rates) {
         for (int k = 0; k < Q; ++k)
             if (!(p->s[k] > 0.0 && p->s[k] < 2.0))
@@ -643,7 +643,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
             else
                 snprintf(g_create_err, sizeof(g_create_err),
                          "lbm_create: kernel %d needs FP64/FP32 storage (kernel 2 with FP64: tile_y <= 8; "
-                         "kernel 3 also takes FP16/BF16 deviations with nx even) and must fit on an SM",
+                         "kernel 3 also takes the 16-bit formats with nx even) and must fit on an SM",
                          p->kernel);
             lbm_destroy(c);
             return LBM_EINVAL;

@@ -25,7 +25,7 @@ cudaError_t launch_step_t(const StepLaunch& c, const void* src, void* dst) {
             }
         }
     }
-    if constexpr (sizeof(typename Codec::S) >= 4 || !Codec::kLocal) {
+    {  // every storage type (16-bit: nx even, checked by the host)
         if (c.kernel == 3) {
             const size_t sm = PipeLayout<Codec, TX, TY>::bytes;
             sc_step_pipe_kernel<Codec, COLL, TX, TY, long long><<<c.grid, TX * TY, sm, c.stream>>>(
@@ -70,7 +70,7 @@ int prepare_async_t(const StepLaunch& c) {
             return e == cudaSuccess ? per_sm : -int(e);
         }
     }
-    if constexpr (sizeof(typename Codec::S) >= 4 || !Codec::kLocal) {
+    {  // every storage type (16-bit: nx even, checked by the host)
         if (c.kernel == 3) {
             using Lay = PipeLayout<Codec, TX, TY>;
             auto kern = sc_step_pipe_kernel<Codec, COLL, TX, TY, long long>;

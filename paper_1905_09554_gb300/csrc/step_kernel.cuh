@@ -661,7 +661,13 @@ struct PipeLayout {
     static constexpr int NSTAGE = 3;
     static constexpr int NSLOT = 4;
     static constexpr size_t stage_bytes = sizeof(HS) * Q * NHALO;
-    static constexpr size_t bytes = NSTAGE * stage_bytes + sizeof(R) * NSLOT * PLANE;
+    // local-reference storage: the ring cells' reference densities (one
+    // float per ring cell and stage) and the density planes (encode targets)
+    static constexpr bool kLocal = Codec::kLocal;
+    static constexpr size_t ref_stage_bytes = kLocal ? sizeof(float) * NHALO : 0;
+    static constexpr size_t rho_ring_bytes = kLocal ? sizeof(float) * NSLOT * PLANE : 0;
+    static constexpr size_t bytes =
+        NSTAGE * (stage_bytes + ref_stage_bytes) + sizeof(R) * NSLOT * PLANE + rho_ring_bytes;
 };
 
 // The 16-bit value in the low (hi = 0) or high (hi = 1) half of a word.
@@ -693,10 +699,13 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src_all, typename Code
     using HS = typename L::HS;
     constexpr int PX = L::PX, PLANE = L::PLANE, NH = L::NHALO;
     static_assert(L::NHALO <= TX * TY, "tile too small for its halo ring");
-    static_assert(!Codec::kLocal, "local-reference storage runs the register-staged kernel");
+    constexpr bool LOCAL = L::kLocal;
+    static_assert(!LOCAL || (L::kWord && !BATCH), "local-reference storage: 16-bit, single lattice");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     HS* hstage = reinterpret_cast<HS*>(smem_raw);  // [NSTAGE][Q][NHALO]
-    R* ring = reinterpret_cast<R*>(smem_raw + L::NSTAGE * L::stage_bytes);
+    R* ring = reinterpret_cast<R*>(smem_raw + L::NSTAGE * L::stage_bytes);  // psi [NSLOT][PLANE]
+    float* rstage = reinterpret_cast<float*>(ring + L::NSLOT * PLANE);        // ring refs [NSTAGE][NHALO]
+    float* rring = rstage + L::NSTAGE * (LOCAL ? NH : 0);                     // rho [NSLOT][PLANE]
 
     const int tid = threadIdx.x;
     const int lx = tid % TX, ly = tid / TX;
@@ -773,6 +782,8 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src_all, typename Code
                     constexpr int q = decltype(qc)::value;
                     async_copy::copy<sizeof(HS)>(st + q * NH + h, base + I(q) * n);
                 });
+                if constexpr (LOCAL)
+                    async_copy::copy<4>(rstage + stage_of(z) * NH + h, a.ref_src + (I(wrapz(z)) * plane + h_xy));
             }
             async_copy::commit();
         };
@@ -780,20 +791,39 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src_all, typename Code
             if (h_slot >= 0) {
                 const HS* st = hstage + stage_of(z) * (Q * NH);
                 R r = R(0);
-                static_for<0, Q>([&](auto qc) {
-                    constexpr int q = decltype(qc)::value;
-                    if constexpr (L::kWord) r += Codec::template decode<q>(half_of<S>(st[q * NH + h], hpar), dev);
-                    else r += Codec::template decode<q>(st[q * NH + h], dev);
-                });
+                if constexpr (LOCAL) {
+                    const float ref = rstage[stage_of(z) * NH + h];
+                    static_for<0, Q>([&](auto qc) {
+                        constexpr int q = decltype(qc)::value;
+                        r += Codec::template decode_ref<q>(half_of<S>(st[q * NH + h], hpar), ref, dev);
+                    });
+                    rring[slot_of(z) * PLANE + h_slot] = r;
+                } else {
+                    static_for<0, Q>([&](auto qc) {
+                        constexpr int q = decltype(qc)::value;
+                        if constexpr (L::kWord)
+                            r += Codec::template decode<q>(half_of<S>(st[q * NH + h], hpar), dev);
+                        else
+                            r += Codec::template decode<q>(st[q * NH + h], dev);
+                    });
+                }
                 ring[slot_of(z) * PLANE + h_slot] = psi_of<R>(r, rho0, inv_rho0);
             }
         };
         auto load_plane = [&](R (&f)[Q], int z) {
             const S* base = src + (I(wrapz(z)) * plane + my_xy);
-            static_for<0, Q>([&](auto qc) {
-                constexpr int q = decltype(qc)::value;
-                f[q] = Codec::template load<q>(base + I(q) * n, dev);
-            });
+            if constexpr (LOCAL) {
+                const float ref = __ldg(a.ref_src + (I(wrapz(z)) * plane + my_xy));
+                static_for<0, Q>([&](auto qc) {
+                    constexpr int q = decltype(qc)::value;
+                    f[q] = Codec::template load_ref<q>(base + I(q) * n, ref, dev);
+                });
+            } else {
+                static_for<0, Q>([&](auto qc) {
+                    constexpr int q = decltype(qc)::value;
+                    f[q] = Codec::template load<q>(base + I(q) * n, dev);
+                });
+            }
         };
         auto own_psi = [&](const R (&f)[Q], int z) {
             R r = R(0);
@@ -802,6 +832,7 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src_all, typename Code
                 r += f[q];
             });
             ring[slot_of(z) * PLANE + my_slot] = psi_of<R>(r, rho0, inv_rho0);
+            if constexpr (LOCAL) rring[slot_of(z) * PLANE + my_slot] = r;
         };
         // One plane: loads of z+2 go out before the collision of z and are
         // consumed after it.  fc holds plane z, fn plane z+1, fl receives z+2;
@@ -835,6 +866,7 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src_all, typename Code
             // loads of z+2 land in fr and are decoded into fc once plane z is
             // stored.  Two arrays alternate.
             S fr[Q];
+            float fref = 0.0f;  // local-reference storage: the prefetched cell's reference
             auto body16 = [&](R (&fc)[Q], int z) {
                 const bool more = z + 2 <= ze;
                 if (more) {
@@ -843,6 +875,7 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src_all, typename Code
                         constexpr int q = decltype(qc)::value;
                         fr[q] = __ldg(base + I(q) * n);
                     });
+                    if constexpr (LOCAL) fref = __ldg(a.ref_src + (I(wrapz(z + 2)) * plane + my_xy));
                     issue_halo(z + 2);
                 } else {
                     async_copy::commit();
@@ -854,14 +887,24 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src_all, typename Code
                     const int zm = (z == 0) ? nz - 1 : z - 1;
                     const int zn = (z + 1 == nz) ? 0 : z + 1;
                     const I zoff[3] = {I(zm) * plane, I(z) * plane, I(zn) * plane};
-                    update_cell<Codec, COLL, PX, I>(fc, ring + slot_of(z - 1) * PLANE, ring + slot_of(z) * PLANE,
-                                                    ring + slot_of(z + 1) * PLANE, my_slot, dst, n, zoff, yoff,
-                                                    xidx, a);
+                    if constexpr (LOCAL) {
+                        const float* rp[3] = {rring + slot_of(z - 1) * PLANE, rring + slot_of(z) * PLANE,
+                                              rring + slot_of(z + 1) * PLANE};
+                        update_cell<Codec, COLL, PX, I>(fc, ring + slot_of(z - 1) * PLANE,
+                                                        ring + slot_of(z) * PLANE, ring + slot_of(z + 1) * PLANE,
+                                                        my_slot, dst, n, zoff, yoff, xidx, a, rp);
+                        a.ref_dst[zoff[1] + my_xy] = rp[1][my_slot];  // this cell's density now
+                    } else {
+                        update_cell<Codec, COLL, PX, I>(fc, ring + slot_of(z - 1) * PLANE,
+                                                        ring + slot_of(z) * PLANE, ring + slot_of(z + 1) * PLANE,
+                                                        my_slot, dst, n, zoff, yoff, xidx, a);
+                    }
                 }
                 if (more) {
                     static_for<0, Q>([&](auto qc) {
                         constexpr int q = decltype(qc)::value;
-                        fc[q] = Codec::template decode<q>(fr[q], dev);
+                        if constexpr (LOCAL) fc[q] = Codec::template decode_ref<q>(fr[q], fref, dev);
+                        else fc[q] = Codec::template decode<q>(fr[q], dev);
                     });
                     own_psi(fc, z + 2);
                 }

@@ -224,7 +224,7 @@ def test_bulk_kernel_needs_fp32_and_nx_multiple_of_4():
         lbm.Lattice(8, 8, 8, storage="f64", kernel=4)
 
 
-@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("storage", ["f16", "bf16", "f16l", "bf16l"])
 @pytest.mark.parametrize("coll", ["srt", "mrt"])
 def test_pipelined_kernel_with_16_bit_storage_is_bit_identical(coll, storage):
     """The pipelined kernel's 16-bit path (ring cells copied as the aligned
@@ -246,7 +246,7 @@ def test_staged_kernels_reject_unsupported_16_bit_layouts():
     with pytest.raises(lbm.LbmError, match="LBM_EINVAL"):
         lbm.Lattice(9, 8, 8, storage="f16", kernel=3)  # nx odd
     with pytest.raises(lbm.LbmError, match="LBM_EINVAL"):
-        lbm.Lattice(8, 8, 8, storage="f16l", kernel=3)
+        lbm.Lattice(9, 8, 8, storage="f16l", kernel=3)  # nx odd
 
 
 @pytest.mark.parametrize("shape", [(1, 1, 32), (1, 1, 1), (5, 1, 1), (1, 7, 3), (2, 3, 2), (33, 1, 2)])

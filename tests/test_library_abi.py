@@ -77,14 +77,15 @@ def test_create_rejects_bad_mrt_rates(lib):
     assert st == lbm.LBM_EINVAL and "rates" in lbm.lbm_last_error(None)
 
 
-def test_local_reference_storage_runs_kernel_1_only(lib):
+def test_local_reference_storage_runs_kernels_1_and_3_only(lib):
     for storage in (lbm.LBM_F16_LOCAL, lbm.LBM_BF16_LOCAL):
         p = lbm.lbm_params_default()
         p.storage = storage
-        p.kernel = 3
-        st, ctx = lbm.lbm_create(p)
-        assert st == lbm.LBM_EINVAL and not ctx.value
-        assert "kernel 1" in lbm.lbm_last_error(None)
+        for kernel in (2, 4, 5):
+            p.kernel = kernel
+            st, ctx = lbm.lbm_create(p)
+            assert st == lbm.LBM_EINVAL and not ctx.value
+            assert "kernel 1 or 3" in lbm.lbm_last_error(None)
 
 
 def test_noalloc_diagnostics_reject_local_reference_storage(lib):
