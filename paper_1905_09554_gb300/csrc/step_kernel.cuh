@@ -713,14 +713,12 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src_all, typename Code
     const DevParams dev = a.dev;
     const int my_slot = (ly + 1) * PX + (lx + 1);
 
-    // Ring cells are spread over all warps in contiguous runs (warp w takes
-    // cells [w*HC, w*HC + HC)), so every warp carries the same extra work
-    // before the per-plane barrier.
-    constexpr int NW = TX * TY / 32, HC = (NH + NW - 1) / NW;
-    static_assert(HC <= 32, "ring run longer than a warp");
+    // Ring cells go to the first NH threads, one each: the ring work then
+    // fills a few whole warps (spreading it over every warp in short runs
+    // measured 33% slower: all warps then issue the ring code with few lanes).
     int hx = 0, hy = 0, h_slot = -1;
-    const int h = (tid / 32) * HC + (tid % 32);
-    if ((tid % 32) < HC && h < NH) {
+    const int h = tid;
+    if (h < NH) {
         if (h < PX) { hx = h - 1; hy = -1; }
         else if (h < 2 * PX) { hx = h - PX - 1; hy = TY; }
         else { const int k = h - 2 * PX; hx = (k < TY) ? -1 : TX; hy = (k < TY) ? k : k - TY; }
@@ -1245,11 +1243,9 @@ sc_step_tma_kernel(const __grid_constant__ CUtensorMap tmap, const float* __rest
     const int my_st = ly * TX + lx;
     bool bad = false;
 
-    constexpr int NW = NT / 32, HC = (NH + NW - 1) / NW;
-    static_assert(HC <= 32, "ring run longer than a warp");
     int hx = 0, hy = 0, h_slot = -1;
-    const int h = (tid / 32) * HC + (tid % 32);
-    if ((tid % 32) < HC && h < NH) {
+    const int h = tid;  // ring cells on the first NH threads, as in the pipelined kernel
+    if (h < NH) {
         if (h < PX) { hx = h - 1; hy = -1; }
         else if (h < 2 * PX) { hx = h - PX - 1; hy = TY; }
         else { const int k = h - 2 * PX; hx = (k < TY) ? -1 : TX; hy = (k < TY) ? k : k - TY; }

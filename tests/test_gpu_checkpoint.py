@@ -41,12 +41,12 @@ def test_resume_is_bit_identical(tmp_path, storage):
         L.save(path)
         L.step(11)
         first = L.get_populations()
-        t_first = L.time()
+        t_first = L.time
         L.load(path)
-        assert L.time() == 7
+        assert L.time == 7
         L.step(11)
         again = L.get_populations()
-        assert L.time() == t_first == 18
+        assert L.time == t_first == 18
     assert np.array_equal(first, again)
     with make(storage) as M:  # a fresh context resumes the same run
         M.load(path)
@@ -77,11 +77,11 @@ def test_damaged_files_are_refused_and_state_kept(tmp_path):
                 fh.write(data)
             st = lbm.lbm_load(L.ctx, bad)
             assert st == lbm.LBM_EIO, name
-            assert L.time() == 8
+            assert L.time == 8
             assert np.array_equal(L.get_populations(), before), name
         assert lbm.lbm_load(L.ctx, str(tmp_path / "missing.ckpt")) == lbm.LBM_EIO
         L.load(path)  # the good file still loads
-        assert L.time() == 5
+        assert L.time == 5
 
 
 def test_mismatched_box_or_storage_is_refused(tmp_path):
@@ -104,5 +104,5 @@ def test_save_replaces_atomically(tmp_path):
         L.save(path)
         L.step(2)
         L.load(path)
-        assert L.time() == 2
+        assert L.time == 2
     assert os.listdir(tmp_path) == ["state.ckpt"]
