@@ -544,11 +544,15 @@ def run_precision(args):
         with lbm.Lattice(nx, ny, nz, G=-5.5, tau=1.0, collision="mrt", rates=rates, storage=f,
                          rho_ref=args.rho_ref) as L:
             L.init_ligament(args.R0, 0.05, rl, rv)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            stream = torch.cuda.current_stream()
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
+            e0.record(stream)
             L.step(200)
+            e1.record(stream)
             torch.cuda.synchronize()
-            res[f]["mlups_200"] = nx * ny * nz * 200 / (time.perf_counter() - t0) / 1e6
+            res[f]["mlups_200"] = nx * ny * nz * 200 / (e0.elapsed_time(e1) / 1e3) / 1e6
+            res[f]["kernel"] = L.kernel_config()
             fields[f] = L.moments()
     for f in fmts[1:]:
         res[f]["err200_rho"] = float(np.abs(fields[f][0] - fields["f64"][0]).max())

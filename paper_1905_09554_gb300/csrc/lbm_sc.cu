@@ -1505,16 +1505,16 @@ static lbm_status ckpt_read_device(lbm_ctx* c, FILE* fp, void* dev, size_t bytes
                                    unsigned char* const (&buf)[2], cudaEvent_t const (&ev)[2], const char* path) {
     char* dst = static_cast<char*>(dev);
     size_t done = 0;
-    bool used[2] = {false, false};
     int k = 0;
     while (done < bytes) {
         const size_t len = bytes - done < kCkptChunk ? bytes - done : kCkptChunk;
-        if (used[k]) LBM_CUDA(c, cudaEventSynchronize(ev[k]));  // the copy out of buf[k] has finished
+        // the copy out of buf[k] (from this call or the previous one) has
+        // finished; an event never recorded completes at once
+        LBM_CUDA(c, cudaEventSynchronize(ev[k]));
         if (fread(buf[k], 1, len, fp) != len) return c->fail(LBM_EIO, "lbm_load: %s is truncated", path);
         fnv.add(buf[k], len);
         LBM_CUDA(c, cudaMemcpyAsync(dst + done, buf[k], len, cudaMemcpyHostToDevice, c->stream));
         LBM_CUDA(c, cudaEventRecord(ev[k], c->stream));
-        used[k] = true;
         done += len;
         k ^= 1;
     }
