@@ -608,11 +608,15 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     // Auto launch shape (measured on GB300 at 256x256x575): FP32 runs the
     // pipelined kernel, on 32x16 tiles for SRT and unit-rate MRT and on 32x4
     // tiles for the other MRT kernels (their collision needs more registers
-    // per cell); the other storage types run the register-staged kernel on
-    // 32x4 tiles.
-    const bool pipe_default = p->storage == LBM_F32;
+    // per cell); the 16-bit formats run the pipelined kernel on 32x4 tiles
+    // when nx is even (FP16 SRT 31.9 GLUPS against 30.4 register-staged;
+    // 32x16 tiles 28.9), else the register-staged kernel; FP64 runs the
+    // register-staged kernel on 32x4 tiles.
+    const bool wide_ok = p->storage == LBM_F32 || p->storage == LBM_F64;
+    const bool pipe_default = p->storage == LBM_F32 || (p->storage >= LBM_F16_DEV && p->nx % 2 == 0);
     const int coll = c->coll;
-    const bool wide = (coll == COLL_SRT || coll == COLL_MRT_UNIT) && (p->kernel == 3 || (p->kernel == 0 && pipe_default));
+    const bool wide = wide_ok && (coll == COLL_SRT || coll == COLL_MRT_UNIT) &&
+                      (p->kernel == 3 || (p->kernel == 0 && pipe_default));
     c->tile_y = p->tile_y ? p->tile_y : ((wide || p->kernel == 5) ? 16 : 4);
     if (p->kernel == 4 && (p->storage != LBM_F32 || p->nx % 4 != 0)) {
         snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel 4 needs FP32 storage and nx %% 4 == 0");
@@ -667,10 +671,14 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     if (p->zchunk) {
         c->zchunk = p->zchunk < p->nz ? p->zchunk : p->nz;
     } else if (c->kernel >= 2) {
-        // about 8 work items per block of the persistent grid, chunks >= 8 planes
+        // at least about 8 work items per block of the persistent grid, and
+        // chunks of 8 to 32 planes: with long chunks the blocks drift apart in
+        // z and neighbouring tiles no longer meet in L2 (measured on GB300 at
+        // 512 x 512 x 1149: 383-plane chunks 25.8 GLUPS, 32-plane 32.5)
         const long long tiles = (long long)tiles_x * tiles_y;
         long long chunks = (8LL * c->grid + tiles - 1) / tiles;
         long long zc = (p->nz + chunks - 1) / chunks;
+        if (zc > 32) zc = 32;
         if (zc < 8) zc = 8;
         c->zchunk = int(zc < p->nz ? zc : p->nz);
     } else {
