@@ -398,11 +398,12 @@ def step_record():
 
 def load_traffic(args, ncell, info):
     """DRAM bytes per launch from the committed ncu record, if it was taken on
-    the current kernel source and this collision/storage/tau/launch shape."""
+    the current kernel source and this collision/storage/tau/launch shape
+    (kernel variant, tile height, z-chunk length)."""
     rec = step_record()
     if rec is None:
         return None
-    key = f"{args.collision}_{args.storage}_tau{args.tau:g}_k{info['kernel']}_ty{info['tile_y']}"
+    key = f"{args.collision}_{args.storage}_tau{args.tau:g}_k{info['kernel']}_ty{info['tile_y']}_zc{info['zchunk']}"
     per = rec.get("bytes_per_cell", {}).get(key)
     return per * ncell if per is not None else None
 

@@ -671,14 +671,25 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     if (p->zchunk) {
         c->zchunk = p->zchunk < p->nz ? p->zchunk : p->nz;
     } else if (c->kernel >= 2) {
-        // at least about 8 work items per block of the persistent grid, and
-        // chunks of 8 to 32 planes: with long chunks the blocks drift apart in
-        // z and neighbouring tiles no longer meet in L2 (measured on GB300 at
-        // 512 x 512 x 1149: 383-plane chunks 25.8 GLUPS, 32-plane 32.5)
+        // At least about 8 work items per block of the persistent grid, and
+        // short chunks: the address range that all blocks touch at once grows
+        // with the chunk length times the plane size.  Measured on GB300, SRT
+        // on 32x16 tiles (GLUPS for chunks of 16 / 32 / 64 planes):
+        // 256^2 x 575 31.8 / 32.0 / 31.9, 576^2 x 1536 30.1 / 29.8 / 28.4,
+        // 640^2 x 1437 30.3 / 26.6 / 25.2, 672^2 x 1792 28.7 / 22.9 / 21.7;
+        // 512^2 x 1149 with 383-plane chunks 25.8.  So at most 32 planes, and
+        // for 32x16 tiles at most 24 MiB of one population's planes (>= 16);
+        // the 32x4 MRT tiles measured best at 32 on the large boxes.
         const long long tiles = (long long)tiles_x * tiles_y;
         long long chunks = (8LL * c->grid + tiles - 1) / tiles;
         long long zc = (p->nz + chunks - 1) / chunks;
-        if (zc > 32) zc = 32;
+        long long zmax = 32;
+        if (c->tile_y >= 16) {
+            const long long plane_bytes = (long long)p->nx * p->ny * (long long)c->elem;
+            zmax = (24LL << 20) / (plane_bytes > 0 ? plane_bytes : 1);
+            zmax = zmax < 16 ? 16 : (zmax > 32 ? 32 : zmax);
+        }
+        if (zc > zmax) zc = zmax;
         if (zc < 8) zc = 8;
         c->zchunk = int(zc < p->nz ? zc : p->nz);
     } else {
