@@ -606,9 +606,10 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     a.dev.scale = float(p->dev_scale);
     a.dev.inv_scale = float(1.0 / p->dev_scale);
     // Auto launch shape (measured on GB300 at 256x256x575): FP32 runs the
-    // pipelined kernel, on 32x16 tiles for SRT and unit-rate MRT and on 32x4
+    // pipelined kernel, on 32x16 tiles for SRT and unit-rate MRT and on 32x8
     // tiles for the other MRT kernels (their collision needs more registers
-    // per cell); the 16-bit formats run the pipelined kernel on 32x4 tiles
+    // per cell: MRT tau = 0.8 gives 26.4 / 27.8 / 26.9 GLUPS on 32x16 / 32x8 /
+    // 32x4); the 16-bit formats run the pipelined kernel on 32x4 tiles
     // when nx is even (FP16 SRT 31.9 GLUPS against 30.4 register-staged;
     // 32x16 tiles 28.9), else the register-staged kernel; FP64 runs the
     // register-staged kernel on 32x4 tiles.
@@ -617,7 +618,9 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     const int coll = c->coll;
     const bool wide = wide_ok && (coll == COLL_SRT || coll == COLL_MRT_UNIT) &&
                       (p->kernel == 3 || (p->kernel == 0 && pipe_default));
-    c->tile_y = p->tile_y ? p->tile_y : ((wide || p->kernel == 5) ? 16 : 4);
+    const bool mrt8 = p->storage == LBM_F32 && (coll == COLL_MRT || coll == COLL_MRT_SPARSE) &&
+                      (p->kernel == 3 || (p->kernel == 0 && pipe_default));
+    c->tile_y = p->tile_y ? p->tile_y : ((wide || p->kernel == 5) ? 16 : (mrt8 ? 8 : 4));
     if (p->kernel == 4 && (p->storage != LBM_F32 || p->nx % 4 != 0)) {
         snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel 4 needs FP32 storage and nx %% 4 == 0");
         lbm_destroy(c);

@@ -680,10 +680,10 @@ __device__ __forceinline__ S half_of(uint32_t w, int hi) {
 }
 
 // Register budget: at most 65536 / (512 threads) = 128 registers per thread
-// so that 512 threads per SM stay resident.  I is the element-offset type:
-// long long for a single lattice (with int offsets this kernel spills at its
-// register budget and measured ~3.5% slower on GB300), int within a batch
-// box (each box's 19 * cells < 2^31; the box offset is applied once).
+// so that 512 threads per SM stay resident.  I is the element-offset type;
+// both the single-lattice and the batch kernels use long long (with int
+// offsets the kernel spills at its register budget: ~3.5% slower for one
+// lattice, ~7% for a batch, measured on GB300).
 //
 // BATCH: the work items span several independent periodic boxes described by
 // b.boxes (geometry and offset of each box's populations in src/dst); the
