@@ -65,10 +65,15 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", choices=["single", "batched", "adjoint", "precision", "paper"], default="single",
+    ap.add_argument("--form", choices=["single", "batched", "adjoint", "precision", "paper", "calibrate"],
+                    default="single",
                     help="single: the sharp-interface ligament; batched: 64 uneven ligaments in one launch per "
                          "step; adjoint: gradients of the neck energy through 500 steps; precision: FP32/FP16/BF16 "
-                         "storage against FP64")
+                         "storage against FP64; paper: the break-up experiment at the paper's parameters; "
+                         "calibrate: the Sec. 3 Laplace / flat-interface / Oh calibration against Tables 1-2")
+    ap.add_argument("--tau0", type=float, default=0.75, help="calibrate form: starting SRT relaxation time")
+    ap.add_argument("--cal-tol", type=float, default=0.01,
+                    help="calibrate form: stop when two consecutive sigma agree to this fraction")
     ap.add_argument("--radii", default="14,28,42",
                     help="paper form: ligament radii of Tables 1-2 to run (14..98)")
     ap.add_argument("--collisions", default="srt,mrt", help="paper form: srt, mrt or both")
@@ -659,9 +664,10 @@ def run_paper(args):
                     if mins[-1] < 0.5 * (rl + rv):
                         broke_at = t
                 if broke_at is not None:
-                    # drops on the axis, for 1.5 t_cap after the pinch-off
+                    # drops on the axis for one t_cap after the pinch-off: the
+                    # paper counts satellites that live about a capillary time
                     drops.append(dg.count_drops(d["maxrho_z"], rl, rv))
-                    if t >= broke_at + 1.5 * tcap:
+                    if t >= broke_at + tcap:
                         break
                 L.step(every)
                 t += every
@@ -672,7 +678,8 @@ def run_paper(args):
         cases.append({"collision": coll, "R0": R0, "eps": eps, "box": [nx, ny, nz], "tau": tau, "t_cap": tcap,
                       "rho_l": rl, "rho_v": rv, "steps": t, "diag_every": every,
                       "drops_max": max(drops) if drops else None, "drops_final": drops[-1] if drops else None,
-                      "satellites": max(0, max(drops) - 2) if drops else None, "paper_satellites": fig_sat,
+                      "satellites": max(0, drops[-1] - 2) if drops else None,
+                      "satellites_transient": max(0, max(drops) - 2) if drops else None, "paper_satellites": fig_sat,
                       "T_break_over_tcap": tb / tcap if tb is not None else None,
                       "paper_T_break": fig_t, "lsa_T_break": lsa_t,
                       "rel_diff": (tb / tcap - fig_t) / fig_t if tb is not None and fig_t else None,
@@ -680,6 +687,59 @@ def run_paper(args):
         print(json.dumps(cases[-1]), flush=True)
     print(json.dumps({"metric": "paper break-up experiment (Fig. 2b) at the paper's parameters",
                       "unit": "T_break / t_cap", "data": "synthetic", "cases": cases}), flush=True)
+
+
+def run_calibrate(args):
+    """The calibration of Sec. 3 at G0 = -5.3, Oh = 0.1, measured with the GPU
+    step: SRT iterates tau -> (Laplace test on droplets of radius 12, 16, 20
+    in an 80^3 box, flat slab) -> the tau that meets Oh, from --tau0 until
+    two consecutive sigma agree to --cal-tol; MRT (rates of Sec. 2) takes one
+    pass at Table 2's tau.  Reports tau, sigma, rho_l, rho_v and t_cap beside
+    Tables 1 and 2."""
+    import numpy as np
+    import torch
+
+    from paper_1905_09554_gb300 import calibration as cal
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    gold = os.path.join(ROOT, "tests", "golden")
+    tables = {"srt": np.loadtxt(os.path.join(gold, "paper_table1_srt.txt")),
+              "mrt": np.loadtxt(os.path.join(gold, "paper_table2_mrt.txt"))}
+    radii = [int(r) for r in args.radii.split(",") if r]
+    G = -5.3
+    cases = []
+    cache = {}
+
+    def measure(coll, tau):
+        key = (coll, round(tau, 6))
+        if key not in cache:
+            rl, rv, _ = cal.flat_coexistence(G, tau, coll, storage="f64")
+            lap = cal.laplace_sigma(G, tau, coll, rho_guess=(rl, rv))
+            cache[key] = (lap["sigma"], rl, rv, lap["fit_r2"])
+        return cache[key]
+
+    t0 = time.perf_counter()
+    for coll in [c for c in args.collisions.split(",") if c]:
+        for R0 in radii:
+            row = [r for r in tables[coll] if int(r[0]) == R0][0]
+            _, Lx, Ly, tau_t, tcap_t, rl_t, rv_t, sig_t = row
+            if coll == "srt":
+                out = cal.calibrate_tau(R0, lambda t: measure("srt", t)[:2], tau0=args.tau0, rel_tol=args.cal_tol)
+                tau = out["tau"]
+                iters = out["iterations"]
+            else:
+                tau, iters = tau_t, 1
+            sig, rl, rv, r2 = measure(coll, tau)
+            tc = cal.t_cap(sig, rl, R0)
+            cases.append({"collision": coll, "R0": R0, "tau": tau, "iterations": iters,
+                          "tau_for_oh": cal.tau_for_oh(0.1, sig, rl, R0),
+                          "sigma": sig, "rho_l": rl, "rho_v": rv, "t_cap": tc, "laplace_fit_r2": r2,
+                          "table": {"tau": tau_t, "sigma": sig_t, "rho_l": rl_t, "rho_v": rv_t, "t_cap": tcap_t},
+                          "rel_diff": {"tau_minus_half": (tau - 0.5) / (tau_t - 0.5) - 1, "sigma": sig / sig_t - 1,
+                                       "rho_l": rl / rl_t - 1, "rho_v": rv / rv_t - 1, "t_cap": tc / tcap_t - 1}})
+            print(json.dumps(cases[-1]), flush=True)
+    print(json.dumps({"metric": "Sec. 3 calibration (Laplace test, flat interface, Oh = 0.1) vs Tables 1-2",
+                      "unit": "relative difference", "data": "synthetic", "G": G,
+                      "wall_s": time.perf_counter() - t0, "cases": cases}), flush=True)
 
 
 def main():
@@ -694,6 +754,8 @@ def main():
         run_precision(args)
     elif args.form == "paper":
         run_paper(args)
+    elif args.form == "calibrate":
+        run_calibrate(args)
     else:
         run_ours(args)
 

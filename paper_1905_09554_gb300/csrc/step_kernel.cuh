@@ -67,14 +67,19 @@ __device__ __forceinline__ void collide_srt(R (&f)[Q], R Fx, R Fy, R Fz, R tau, 
     const R uz = (jz + tau * Fz) * inv_rho;
     const R usq = R(1.5) * (ux * ux + uy * uy + uz * uz);
     const R base = R(1) - usq;
-    f[0] += omega * (R(wq(0)) * rho * base - f[0]);
+    // w_a rho per speed shell, the rest one from sum_a w_a = 1: the rounded
+    // weights float(1/3) + 6 float(1/18) + 12 float(1/36) sum to 1 + 3e-8,
+    // which made FP32 runs gain ~3e-8 of their mass every step.
+    const R r1 = R(wq(1)) * rho, r2 = R(wq(7)) * rho;
+    const R r0 = rho - R(6) * r1 - R(12) * r2;
+    f[0] += omega * (r0 * base - f[0]);
     static_for<0, 9>([&](auto pc) {
         constexpr int q = 2 * decltype(pc)::value + 1;
         R cu = R(0);
         if constexpr (cx(q) != 0) cu += R(cx(q)) * ux;
         if constexpr (cy(q) != 0) cu += R(cy(q)) * uy;
         if constexpr (cz(q) != 0) cu += R(cz(q)) * uz;
-        const R wr = R(wq(q)) * rho;
+        const R wr = (wq(q) == wq(1)) ? r1 : r2;
         const R A = wr * (base + R(4.5) * cu * cu);
         const R B = wr * (R(3) * cu);
         f[q] += omega * ((A + B) - f[q]);
@@ -261,7 +266,11 @@ __device__ __forceinline__ void collide_mrt_sparse(R (&f)[Q], R Fx, R Fy, R Fz, 
         return acc;
     };
     const R base = R(1) - R(1.5) * u2;
-    f[0] = R(wq(0)) * (rho * base - R(1.5) * uF) + corr(std::integral_constant<int, 0>{});
+    // w_a rho per speed shell, the rest one from sum_a w_a = 1 (as in
+    // collide_srt: no systematic mass from the rounded weights)
+    const R r1 = R(wq(1)) * rho, r2 = R(wq(7)) * rho;
+    const R r0 = rho - R(6) * r1 - R(12) * r2;
+    f[0] = r0 * base - R(wq(0)) * R(1.5) * uF + corr(std::integral_constant<int, 0>{});
     static_for<0, 9>([&](auto pc) {
         constexpr int q = 2 * decltype(pc)::value + 1;
         R cu = R(0), cF = R(0);
@@ -269,9 +278,10 @@ __device__ __forceinline__ void collide_mrt_sparse(R (&f)[Q], R Fx, R Fy, R Fz, 
         if constexpr (cy(q) != 0) { cu += R(cy(q)) * uy; cF += R(cy(q)) * Fy; }
         if constexpr (cz(q) != 0) { cu += R(cz(q)) * uz; cF += R(cz(q)) * Fz; }
         const R w = R(wq(q));
+        const R wr = (wq(q) == wq(1)) ? r1 : r2;
         // f_eq = A +/- B; Guo source S/2 = E +/- O
-        const R A = w * rho * (base + R(4.5) * cu * cu);
-        const R B = w * rho * (R(3) * cu);
+        const R A = wr * (base + R(4.5) * cu * cu);
+        const R B = wr * (R(3) * cu);
         const R E = w * (R(-1.5) * uF + R(4.5) * cu * cF);
         const R O = w * (R(1.5) * cF);
         const R c = corr(std::integral_constant<int, q>{});  // even rows: equal on both members
