@@ -48,20 +48,10 @@ slice_diag_noalloc_kernel(double* __restrict__ scratch, const typename Codec::S*
     __shared__ double red[7][kThreads];
     const int z = blockIdx.x;
     const long long plane = (long long)nx * ny;
-    const typename Codec::S* fz = f + z * plane;
-    double m = 0, jx = 0, jy = 0, jz = 0, area = 0, mx = 0, bad = 0;
-    const double inv = 1.0 / (rho_l - rho_v);
-    for (long long i = threadIdx.x; i < plane; i += kThreads) {
-        double r, ax, ay, az;
-        diag_cell<Codec>(fz + i, n, dev, r, ax, ay, az);
-        m += r;
-        jx += ax;
-        jy += ay;
-        jz += az;
-        area += fmin(fmax((r - rho_v) * inv, 0.0), 1.0);
-        mx = fmax(mx, r);
-        if (!(r > 0.0) || !isfinite(r)) bad += 1.0;
-    }
+    double acc[7];
+    diag_accumulate<Codec>(f + z * plane, n, plane, threadIdx.x, kThreads, dev, rho_v, 1.0 / (rho_l - rho_v),
+                           nullptr, acc);
+    const double m = acc[0], jx = acc[1], jy = acc[2], jz = acc[3], area = acc[4], mx = acc[5], bad = acc[6];
     red[0][threadIdx.x] = m;
     red[1][threadIdx.x] = jx;
     red[2][threadIdx.x] = jy;
