@@ -190,11 +190,12 @@ __global__ void ref_sum_kernel(float* __restrict__ ref, double* __restrict__ acc
 template <class Codec>
 __global__ void density_kernel(double* __restrict__ rho, const typename Codec::S* __restrict__ f,
                                long long n, DevParams dev, const float* ref) {
+    // rho summed in the storage's arithmetic type, as the step kernel does
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        double r = 0.0;
-        for (int q = 0; q < Q; ++q) r += dec<Codec>(f + q * n + i, q, ref, i, dev);
-        rho[i] = r;
+        typename Codec::R r, jx, jy, jz;
+        diag_cell<Codec>(f + i, n, dev, Codec::kLocal ? ref[i] : 0.0f, r, jx, jy, jz);
+        rho[i] = double(r);
     }
 }
 
@@ -904,12 +905,18 @@ lbm_status lbm_moments(lbm_ctx* c, double* rho, double* ux, double* uy, double* 
         d_uy = uy;
         d_uz = uz;
     } else {
-        lbm_status s = ensure_scratch(c, 4 * nb);
+        // staging for the requested fields only (rho always: u needs it)
+        const int nf = 1 + (ux ? 1 : 0) + (uy ? 1 : 0) + (uz ? 1 : 0);
+        lbm_status s = ensure_scratch(c, nf * nb);
         if (s != LBM_OK) return s;
-        d_rho = c->scratch;
-        d_ux = ux ? c->scratch + c->n : nullptr;
-        d_uy = uy ? c->scratch + 2 * c->n : nullptr;
-        d_uz = uz ? c->scratch + 3 * c->n : nullptr;
+        double* next = c->scratch;
+        d_rho = next;
+        next += c->n;
+        d_ux = ux ? next : nullptr;
+        next += ux ? c->n : 0;
+        d_uy = uy ? next : nullptr;
+        next += uy ? c->n : 0;
+        d_uz = uz ? next : nullptr;
     }
     const int blocks = grid_for(c->n, 256, c->num_sms);
     const auto& p = c->p;

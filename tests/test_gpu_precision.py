@@ -107,8 +107,8 @@ def test_local_storage_round_trip(fmt, scale):
     assert np.mean(got == want) > 0.95
     # the deviations are only the 1% noise: the stored error is tiny
     assert np.abs(got - f).max() <= (2 * EPS[fmt] * np.abs(d).max() + sub) / scale + 4e-7 * R.max()
-    # moments decode with the same per-cell reference
-    assert np.abs(got_rho - got.sum(axis=0)).max() <= 1e-6 * RL
+    # moments decode with the same per-cell reference (rho summed in float)
+    assert np.abs(got_rho - got.sum(axis=0)).max() <= 5e-6 * RL
 
 
 @pytest.mark.parametrize("fmt", ["f16l", "bf16l"])
