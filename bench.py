@@ -71,6 +71,9 @@ def parse_args():
                          "step; adjoint: gradients of the neck energy through 500 steps; precision: FP32/FP16/BF16 "
                          "storage against FP64; paper: the break-up experiment at the paper's parameters; "
                          "calibrate: the Sec. 3 Laplace / flat-interface / Oh calibration against Tables 1-2")
+    ap.add_argument("--series", action="store_true",
+                    help="paper form: also report the neck-radius and perturbation time series, the interface "
+                         "silhouettes at t* = 7, 8, 9 and the linearity of the final pinch")
     ap.add_argument("--tau0", type=float, default=0.75, help="calibrate form: starting SRT relaxation time")
     ap.add_argument("--cal-tol", type=float, default=0.01,
                     help="calibrate form: stop when two consecutive sigma agree to this fraction")
@@ -651,6 +654,7 @@ def run_paper(args):
         with lbm.Lattice(nx, ny, nz, G=-5.3, tau=tau, collision=coll, storage="f32") as L:
             L.init_ligament(float(R0), eps, rl, rv, n_waves=2)
             ts, mins, drops = [], [], []
+            necks, amps, sil = [], [], {}
             t, broke_at = 0, None
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -661,6 +665,12 @@ def run_paper(args):
                 if broke_at is None:
                     ts.append(t)
                     mins.append(float(d["maxrho_z"].min()))
+                    if args.series:
+                        necks.append(dg.neck_radius(d["area_z"]) / R0)
+                        amps.append(dg.mode_amplitude(d["area_z"], n_waves=2))
+                        for ts_star in (7, 8, 9):  # silhouettes R(z)/R0 at the first sample past t* (Fig. 5b)
+                            if ts_star not in sil and t >= ts_star * tcap:
+                                sil[ts_star] = [round(float(v) / R0, 4) for v in dg.equivalent_radius(d["area_z"])]
                     if mins[-1] < 0.5 * (rl + rv):
                         broke_at = t
                 if broke_at is not None:
@@ -684,6 +694,25 @@ def run_paper(args):
                       "paper_T_break": fig_t, "lsa_T_break": lsa_t,
                       "rel_diff": (tb / tcap - fig_t) / fig_t if tb is not None and fig_t else None,
                       "wall_s": wall, "glups": nx * ny * nz * t / wall / 1e9, "kernel": cfg})
+        if args.series and ts:
+            tt = np.asarray(ts[:len(necks)], dtype=float) / tcap
+            nk = np.asarray(necks)
+            a0 = amps[0] if amps and amps[0] != 0 else 1.0
+            # final pinch (Fig. 6): R_min / R0 against t* where it falls from 0.3 to 0.05
+            sel = (nk <= 0.3) & (nk >= 0.05)
+            pinch = None
+            if sel.sum() >= 3:
+                sl, ic = np.polyfit(tt[sel], nk[sel], 1)
+                fit = sl * tt[sel] + ic
+                ss = float(((nk[sel] - nk[sel].mean()) ** 2).sum())
+                pinch = {"slope_R0_per_tcap": float(sl), "points": int(sel.sum()),
+                         "r2": 1.0 - float(((nk[sel] - fit) ** 2).sum()) / ss if ss > 0 else 1.0}
+            cases[-1]["series"] = {"t_star": [round(float(v), 4) for v in tt],
+                                   "neck_over_R0": [round(float(v), 4) for v in nk],
+                                   "mode_amplitude_over_initial": [round(float(v) / a0, 4) for v in amps],
+                                   "silhouettes_R_over_R0": {str(k): v for k, v in sil.items()},
+                                   "pinch_linear_fit": pinch}
+            print(json.dumps({"collision": coll, "R0": R0, "eps": eps, "pinch_linear_fit": pinch}), flush=True)
         print(json.dumps(cases[-1]), flush=True)
     print(json.dumps({"metric": "paper break-up experiment (Fig. 2b) at the paper's parameters",
                       "unit": "T_break / t_cap", "data": "synthetic", "cases": cases}), flush=True)
