@@ -91,9 +91,15 @@ typedef struct {
                              population copies (each 19*nx*ny*nz elements of the
                              storage type, 16-byte aligned); NULL = the library
                              allocates (and frees them in lbm_destroy).            */
-    int zchunk;           /* step kernel: z planes per thread block; 0 = auto       */
-    int tile_y;           /* step kernel: tile height (4, 8 or 16); 0 = auto        */
-    int kernel;           /* step kernel variant: 0 = auto, 1 = register-staged,
+    int zchunk;           /* step kernel: z planes per work item; 0 = auto (at most
+                             32, and at most 24 MiB of one population's planes
+                             on 32x16 tiles)                                        */
+    int tile_y;           /* step kernel: tile height (4, 8 or 16); 0 = auto: 16
+                             for FP32 SRT and unit-rate MRT, 8 for other FP32
+                             MRT, 4 otherwise                                       */
+    int kernel;           /* step kernel variant: 0 = auto (3 for FP32, and for
+                             the 16-bit formats when nx is even; else 1),
+                             1 = register-staged,
                              2 = cp.async-staged persistent, 3 = pipelined
                              persistent (2: FP64/FP32 storage; 3: also the
                              16-bit formats when nx is even),
