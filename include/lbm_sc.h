@@ -107,11 +107,24 @@ typedef struct {
                              5 = tensor-copy pipeline (FP32, tile_y 8 or 16,
                              nx % 32 == 0, ny % tile_y == 0; steps on buffers
                              other than the two copies, e.g. the adjoint's
-                             recomputation, run kernel 3)                           */
+                             recomputation, run kernel 3),
+                             6 = two-belt force (chosen when G2 != 0)               */
     int test_stall;       /* test only: with kernel 4 the copy warp issues nothing,
                              so every bounded wait times out (about 1 s) and the
                              next lbm_diag / lbm_moments / lbm_get_populations
                              returns LBM_ETIMEOUT.  0 in normal use.               */
+    double G2;            /* second belt of the two-belt (multirange) force that
+                             Sec. 2 names (0 = Eq. SC_force alone):
+                             F = -psi(x) [G sum_{D3Q19} w_a psi(x + c_a) c_a
+                               + G2 sum_{E8} (p_b / 3) psi(x + e_b) e_b],
+                             E8 = the 92 vectors with components in {-2..2} and
+                             |e|^2 in {1,2,3,4,5,6,8}, p per shell 4/45, 1/21,
+                             2/105, 5/504, 1/315, 1/630, 1/5040 (isotropic to 8th
+                             order).  Bulk EoS P = rho cs2 + cs2 (G + G2) psi^2/2;
+                             the split of G + G2 sets the surface tension.  Runs
+                             kernel 6 (register-staged, two-cell psi halo, 32x8
+                             tiles) with FP64/FP32 storage; not available to
+                             batches or the adjoint.                               */
 } lbm_params;
 
 /* Fill *p with defaults: D3Q19, 32^3, G = -5.5, SRT tau = 1, psi exp, rho0 = 1,

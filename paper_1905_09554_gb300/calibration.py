@@ -33,11 +33,12 @@ import numpy as np
 CS2 = 1.0 / 3.0
 
 
-def pressure(rho, G, rho0=1.0):
-    """Bulk pressure of the Shan-Chen fluid, Eq. EOS_SC."""
+def pressure(rho, G, rho0=1.0, G2=0.0):
+    """Bulk pressure of the Shan-Chen fluid, Eq. EOS_SC; with the two-belt
+    force the interaction strength is G + G2."""
     rho = np.asarray(rho, dtype=float)
     psi = rho0 * (1.0 - np.exp(-rho / rho0))
-    return CS2 * rho + 0.5 * CS2 * G * psi ** 2
+    return CS2 * rho + 0.5 * CS2 * (G + G2) * psi ** 2
 
 
 def tau_for_oh(Oh, sigma, rho_l, R0):
@@ -67,14 +68,14 @@ def _run_to_steady(L, max_steps, check_every, tol):
     return rho_prev, steps
 
 
-def _lattice(shape, G, tau, collision, rates, storage):
+def _lattice(shape, G, tau, collision, rates, storage, G2=0.0):
     from . import lbm
     nx, ny, nz = shape
-    return lbm.Lattice(nx, ny, nz, G=G, tau=tau, collision=collision, rates=rates, storage=storage)
+    return lbm.Lattice(nx, ny, nz, G=G, tau=tau, collision=collision, rates=rates, storage=storage, G2=G2)
 
 
 def flat_coexistence(G, tau, collision="srt", rates=None, storage="f64", length=64, width=2.0,
-                     rho_guess=(2.1, 0.1), max_steps=40000, check_every=500, tol=1e-10):
+                     rho_guess=(2.1, 0.1), max_steps=40000, check_every=500, tol=1e-10, G2=0.0):
     """Coexistence densities from a flat liquid slab (normal along z) in a
     4 x 4 x length periodic box: (rho_l, rho_v, steps)."""
     rl, rv = rho_guess
@@ -82,7 +83,7 @@ def flat_coexistence(G, tau, collision="srt", rates=None, storage="f64", length=
     d = np.abs(z - (length - 1) / 2.0) - length / 4.0  # < 0 inside the slab
     prof = rv + 0.5 * (rl - rv) * (1.0 - np.tanh(d / width))
     rho0 = np.broadcast_to(prof[:, None, None], (length, 4, 4)).copy()
-    with _lattice((4, 4, length), G, tau, collision, rates, storage) as L:
+    with _lattice((4, 4, length), G, tau, collision, rates, storage, G2) as L:
         L.set_density(rho0)
         rho, steps = _run_to_steady(L, max_steps, check_every, tol)
     col = rho[:, 0, 0]
@@ -91,7 +92,7 @@ def flat_coexistence(G, tau, collision="srt", rates=None, storage="f64", length=
 
 def laplace_sigma(G, tau, collision="srt", rates=None, storage="f64", radii=(16.0, 20.0, 24.0),
                   box_factor=4.0, width=2.0, rho_guess=(2.1, 0.1), max_steps=30000, check_every=1000,
-                  tol=1e-9):
+                  tol=1e-9, G2=0.0):
     """Surface tension from the Laplace test on static droplets.
 
     Each droplet of initial radius R sits in a periodic box of about
@@ -116,7 +117,7 @@ def laplace_sigma(G, tau, collision="srt", rates=None, storage="f64", radii=(16.
         g = np.arange(box) - c
         r = np.sqrt(g[:, None, None] ** 2 + g[None, :, None] ** 2 + g[None, None, :] ** 2)
         rho0 = rv + 0.5 * (rl - rv) * (1.0 - np.tanh((r - R) / width))
-        with _lattice((box, box, box), G, tau, collision, rates, storage) as L:
+        with _lattice((box, box, box), G, tau, collision, rates, storage, G2) as L:
             L.set_density(rho0)
             rho, steps = _run_to_steady(L, max_steps, check_every, tol)
         k = box // 2
@@ -126,7 +127,7 @@ def laplace_sigma(G, tau, collision="srt", rates=None, storage="f64", radii=(16.
         V = float(box) ** 3
         Vl = (float(rho.sum()) - rho_out * V) / (rho_in - rho_out)
         Rs.append((3.0 * Vl / (4.0 * math.pi)) ** (1.0 / 3.0))
-        dps.append(float(pressure(rho_in, G) - pressure(rho_out, G)))
+        dps.append(float(pressure(rho_in, G, G2=G2) - pressure(rho_out, G, G2=G2)))
         rins.append(rho_in)
         routs.append(rho_out)
         steps_all.append(steps)

@@ -15,6 +15,7 @@
 #include "../../include/lbm_sc.h"
 #include "codec.cuh"
 #include "diag_cell.cuh"
+#include "e8.cuh"
 #include "lattice.cuh"
 #include "step_args.h"
 #include "adjoint.h"
@@ -201,10 +202,16 @@ __global__ void density_kernel(double* __restrict__ rho, const typename Codec::S
 
 // u_b = (j + F/2)/rho with F from Eq. SC_force evaluated on the density
 // field `rho` (float64), j from the populations.
+__device__ __forceinline__ int wrap_periodic(int i, int n) {  // periodic index, any offset
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
 template <class Codec>
 __global__ void velocity_kernel(double* __restrict__ ux, double* __restrict__ uy, double* __restrict__ uz,
                                 const double* __restrict__ rho, const typename Codec::S* __restrict__ f,
-                                int nx, int ny, int nz, double G, double rho0, DevParams dev, const float* ref) {
+                                int nx, int ny, int nz, double G, double G2, double rho0, DevParams dev,
+                                const float* ref) {
     const long long n = (long long)nx * ny * nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -230,8 +237,24 @@ __global__ void velocity_kernel(double* __restrict__ ux, double* __restrict__ uy
                 sz += wq(q) * cz(q) * psn;
             }
         });
+        sx *= G;
+        sy *= G;
+        sz *= G;
+        if (G2 != 0.0) {  // second belt of the two-belt force: E8 vectors, weights p/3
+            static_for<0, mr::kNE>([&](auto kc) {
+                constexpr mr::Vec e = mr::e8(decltype(kc)::value);
+                constexpr double pw = mr::p_e8(e.x * e.x + e.y * e.y + e.z * e.z) / 3.0;
+                const int xx = wrap_periodic(x + e.x, nx), yy = wrap_periodic(y + e.y, ny),
+                          zz = wrap_periodic(z + e.z, nz);
+                const double rn = rho[((long long)zz * ny + yy) * nx + xx];
+                const double psn = G2 * pw * rho0 * (1.0 - exp(-rn / rho0));
+                if constexpr (e.x != 0) sx += e.x * psn;
+                if constexpr (e.y != 0) sy += e.y * psn;
+                if constexpr (e.z != 0) sz += e.z * psn;
+            });
+        }
         const double r = rho[i];
-        const double g = -G * rho0 * (1.0 - exp(-r / rho0));
+        const double g = -rho0 * (1.0 - exp(-r / rho0));
         if (ux) ux[i] = (jx + 0.5 * g * sx) / r;
         if (uy) uy[i] = (jy + 0.5 * g * sy) / r;
         if (uz) uz[i] = (jz + 0.5 * g * sz) / r;
@@ -473,6 +496,13 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
         return create_fail(LBM_EINVAL, "lbm_create: unknown collision operator");
     if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return create_fail(LBM_EINVAL, "lbm_create: tau must be > 0.5");
     if (!std::isfinite(p->G)) return create_fail(LBM_EINVAL, "lbm_create: G must be finite");
+    if (!std::isfinite(p->G2)) return create_fail(LBM_EINVAL, "lbm_create: G2 must be finite");
+    if (p->G2 != 0.0 && ((p->storage != LBM_F64 && p->storage != LBM_F32) || (p->kernel != 0 && p->kernel != 6) ||
+                         (p->tile_y != 0 && p->tile_y != 8)))
+        return create_fail(LBM_EINVAL,
+                           "lbm_create: the two-belt force (G2 != 0) runs kernel 6 on 32x8 tiles with FP64/FP32 storage");
+    if (p->G2 == 0.0 && p->kernel == 6)
+        return create_fail(LBM_EINVAL, "lbm_create: kernel 6 is the two-belt force kernel (needs G2 != 0)");
     if (p->psi != LBM_PSI_EXP) return create_fail(LBM_EINVAL, "lbm_create: unknown psi law");
     if (!(p->rho0 > 0) || !std::isfinite(p->rho0)) return create_fail(LBM_EINVAL, "lbm_create: rho0 must be > 0");
     if (p->storage < LBM_F64 || p->storage > LBM_BF16_LOCAL) return create_fail(LBM_EINVAL, "lbm_create: unknown storage");
@@ -575,6 +605,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     a.nz = p->nz;
     a.n = n;
     a.G = p->G;
+    a.G2 = p->G2;
     a.tau = p->tau;
     a.omega = 1.0 / p->tau;
     a.rho0 = p->rho0;
@@ -610,6 +641,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     const bool mrt8 = p->storage == LBM_F32 && (coll == COLL_MRT || coll == COLL_MRT_SPARSE) &&
                       (p->kernel == 3 || (p->kernel == 0 && pipe_default));
     c->tile_y = p->tile_y ? p->tile_y : ((wide || p->kernel == 5) ? 16 : (mrt8 ? 8 : 4));
+    if (p->G2 != 0.0) c->tile_y = 8;  // the two-belt kernel
     if (p->kernel == 4 && (p->storage != LBM_F32 || p->nx % 4 != 0)) {
         snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel 4 needs FP32 storage and nx %% 4 == 0");
         lbm_destroy(c);
@@ -621,13 +653,13 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
         lbm_destroy(c);
         return LBM_EINVAL;
     }
-    if (p->kernel < 0 || p->kernel > 5) {
-        snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel must be 0 .. 5");
+    if (p->kernel < 0 || p->kernel > 6) {
+        snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel must be 0 .. 6");
         lbm_destroy(c);
         return LBM_EINVAL;
     }
-    c->kernel = 1;
-    if (p->kernel != 1 && !(p->kernel == 0 && !pipe_default)) {
+    c->kernel = p->G2 != 0.0 ? 6 : 1;
+    if (p->G2 == 0.0 && p->kernel != 1 && !(p->kernel == 0 && !pipe_default)) {
         c->kernel = p->kernel == 0 ? 3 : p->kernel;
         const int per_sm = prepare_async(c);
         if (per_sm > 0) {
@@ -662,7 +694,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     const int tiles_x = (p->nx + 31) / 32, tiles_y = (p->ny + c->tile_y - 1) / c->tile_y;
     if (p->zchunk) {
         c->zchunk = p->zchunk < p->nz ? p->zchunk : p->nz;
-    } else if (c->kernel >= 2) {
+    } else if (c->kernel >= 2 && c->kernel != 6) {
         // At least about 8 work items per block of the persistent grid, and
         // short chunks: the address range that all blocks touch at once grows
         // with the chunk length times the plane size.  Measured on GB300, SRT
@@ -744,7 +776,7 @@ lbm_status lbm_kernel_config(const lbm_ctx* c, int* kernel, int* tile_y, int* zc
     if (tile_y) *tile_y = c->tile_y;
     if (zchunk) *zchunk = c->zchunk;
     if (grid) {
-        if (c->kernel >= 2) {
+        if (c->kernel >= 2 && c->kernel != 6) {
             *grid = c->grid;
         } else {
             const StepArgs& a = c->args;
@@ -925,7 +957,7 @@ lbm_status lbm_moments(lbm_ctx* c, double* rho, double* ux, double* uy, double* 
         const auto* f = static_cast<const typename C::S*>(c->f[c->cur]);
         density_kernel<C><<<blocks, 256, 0, c->stream>>>(d_rho, f, c->n, c->args.dev, c->ref[c->cur]);
         if (d_ux || d_uy || d_uz)
-            velocity_kernel<C><<<blocks, 256, 0, c->stream>>>(d_ux, d_uy, d_uz, d_rho, f, p.nx, p.ny, p.nz, p.G,
+            velocity_kernel<C><<<blocks, 256, 0, c->stream>>>(d_ux, d_uy, d_uz, d_rho, f, p.nx, p.ny, p.nz, p.G, p.G2,
                                                               p.rho0, c->args.dev, c->ref[c->cur]);
         return 0;
     });
@@ -1107,6 +1139,7 @@ lbm_status lbm_batch_create(const lbm_params* p, int count, const int* dims, lbm
     if (!p || !dims || count < 1) return create_fail(LBM_EINVAL, "lbm_batch_create: need params, dims and count >= 1");
     if (p->storage != LBM_F32 && p->storage != LBM_F64)
         return create_fail(LBM_EINVAL, "lbm_batch_create: batches support FP32 and FP64 storage");
+    if (p->G2 != 0.0) return create_fail(LBM_EINVAL, "lbm_batch_create: batches use the single-belt force (G2 = 0)");
     if (p->f_a || p->f_b) return create_fail(LBM_EINVAL, "lbm_batch_create: the batch allocates its own copies");
     lbm_batch* b = new (std::nothrow) lbm_batch();
     if (!b) return create_fail(LBM_ENOMEM, "lbm_batch_create: host allocation failed");
@@ -1332,6 +1365,8 @@ lbm_status lbm_adjoint_forward(lbm_ctx* c, const double* rho0, int on_device, lo
         return c->fail(LBM_EUNSUPPORTED, "lbm_adjoint_forward: the adjoint covers the SRT operator only");
     if (c->p.storage != LBM_F32 && c->p.storage != LBM_F64)
         return c->fail(LBM_EUNSUPPORTED, "lbm_adjoint_forward: FP32 or FP64 storage only");
+    if (c->p.G2 != 0.0)
+        return c->fail(LBM_EUNSUPPORTED, "lbm_adjoint_forward: the adjoint covers the single-belt force only");
     if (!rho0 || nsteps < 1 || every < 1) return c->fail(LBM_EINVAL, "lbm_adjoint_forward: need rho0, n >= 1, every >= 1");
     auto& A = c->adj;
     const size_t state = (size_t)Q * (size_t)c->n * c->elem;

@@ -20,7 +20,8 @@ struct StepArgs {
     int tiles_x, n_tiles; // xy tiles of the persistent kernel
     int n_items;          // n_tiles * number of z chunks
     long long n;          // cells = nx*ny*nz (population stride)
-    double G;             // interaction strength G0
+    double G;             // interaction strength G0 (first belt)
+    double G2;            // second-belt strength of the two-belt force (kernel 6)
     double tau, omega;    // SRT relaxation time and 1/tau
     double rho0, inv_rho0;
     double s[Q];          // MRT rates, moment order
@@ -51,7 +52,7 @@ struct BatchArgs {
 struct StepLaunch {
     StepArgs args;
     int kernel;           // 1 register-staged, 2 cp.async-staged, 3 pipelined,
-                          // 4 bulk-copy, 5 tensor-copy
+                          // 4 bulk-copy, 5 tensor-copy, 6 two-belt force
     const CUtensorMap* tmap;  // kernel 5: tensor map of the source copy
     int tile_y;           // 4, 8 or 16 (tile width is 32)
     int grid;             // persistent grid (kernels 2 and 3)

@@ -55,6 +55,7 @@ class lbm_params(ctypes.Structure):
         ("tile_y", ctypes.c_int),
         ("kernel", ctypes.c_int),
         ("test_stall", ctypes.c_int),
+        ("G2", ctypes.c_double),
     ]
 
 
@@ -304,7 +305,7 @@ class Lattice:
 
     def __init__(self, nx, ny, nz, G=-5.5, tau=1.0, collision="srt", rates=None,
                  storage="f32", rho0=1.0, rho_ref=1.0, dev_scale=1.0,
-                 torch_buffers=True, stream=None, zchunk=0, tile_y=0, kernel=0, test_stall=0):
+                 torch_buffers=True, stream=None, zchunk=0, tile_y=0, kernel=0, test_stall=0, G2=0.0):
         lib = load()
         p = lbm_params_default()
         p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
@@ -318,6 +319,7 @@ class Lattice:
         p.rho_ref, p.dev_scale = float(rho_ref), float(dev_scale)
         p.zchunk, p.tile_y, p.kernel = int(zchunk), int(tile_y), int(kernel)
         p.test_stall = int(test_stall)
+        p.G2 = float(G2)
         self.shape = (int(nz), int(ny), int(nx))
         self.n = int(nx) * int(ny) * int(nz)
         self.storage = storage
