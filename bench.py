@@ -12,7 +12,7 @@ are far larger than L2, so no flush is needed between steps.
 Prints ONE JSON line (rank 0).  `value` is MLUPS (million lattice updates per
 second) over all ranks, device-timed with CUDA events; `e2e` is the same
 metric through the C ABI with host buffers (initial density uploaded from
-pinned host memory, diagnostics read back every 10 steps, final density read
+pinned host memory, diagnostics read back every 50 steps, final density read
 back); `roofline` relates the step kernel's algorithmic bytes to the measured
 HBM copy bandwidth; `cpu_baseline` times the FP64 reference implementation on
 a bounded slab of the same workload on the host cores.
@@ -62,7 +62,10 @@ def parse_args():
     ap.add_argument("--tile-y", type=int, default=0)
     ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 register-staged, 2 cp.async-staged, 3 pipelined, 4 bulk-copy, "
                          "5 tensor-copy")
-    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--e2e-steps", type=int, default=1000)
+    ap.add_argument("--e2e-diag-every", type=int, default=50,
+                    help="e2e: steps between diagnostics read back to the host (the paper's break-up runs "
+                         "sample every t_cap/40, 63 steps for the R0 = 64 ligament)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--form", choices=["single", "batched", "adjoint", "precision", "paper", "calibrate", "multirange"],
@@ -318,7 +321,7 @@ def run_ours(args):
         from paper_1905_09554_gb300 import inputs
         rho_host.numpy()[...] = inputs.ligament_density(nx, ny, nz, args.R0, 0.05, w["rho_l"], w["rho_v"])
         rho_out = torch.empty((nz, ny, nx), dtype=torch.float64, pin_memory=True)
-        diag_every = 10
+        diag_every = args.e2e_diag_every
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
