@@ -498,9 +498,9 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     if (!std::isfinite(p->G)) return create_fail(LBM_EINVAL, "lbm_create: G must be finite");
     if (!std::isfinite(p->G2)) return create_fail(LBM_EINVAL, "lbm_create: G2 must be finite");
     if (p->G2 != 0.0 && ((p->storage != LBM_F64 && p->storage != LBM_F32) || (p->kernel != 0 && p->kernel != 6) ||
-                         (p->tile_y != 0 && p->tile_y != 8)))
-        return create_fail(LBM_EINVAL,
-                           "lbm_create: the two-belt force (G2 != 0) runs kernel 6 on 32x8 tiles with FP64/FP32 storage");
+                         (p->tile_y != 0 && p->tile_y != 8 && p->tile_y != 16)))
+        return create_fail(LBM_EINVAL, "lbm_create: the two-belt force (G2 != 0) runs kernel 6 on 32x8 or 32x16 "
+                                       "tiles with FP64/FP32 storage");
     if (p->G2 == 0.0 && p->kernel == 6)
         return create_fail(LBM_EINVAL, "lbm_create: kernel 6 is the two-belt force kernel (needs G2 != 0)");
     if (p->psi != LBM_PSI_EXP) return create_fail(LBM_EINVAL, "lbm_create: unknown psi law");
@@ -641,7 +641,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     const bool mrt8 = p->storage == LBM_F32 && (coll == COLL_MRT || coll == COLL_MRT_SPARSE) &&
                       (p->kernel == 3 || (p->kernel == 0 && pipe_default));
     c->tile_y = p->tile_y ? p->tile_y : ((wide || p->kernel == 5) ? 16 : (mrt8 ? 8 : 4));
-    if (p->G2 != 0.0) c->tile_y = 8;  // the two-belt kernel
+    if (p->G2 != 0.0) c->tile_y = p->tile_y ? p->tile_y : 8;  // the two-belt kernel
     if (p->kernel == 4 && (p->storage != LBM_F32 || p->nx % 4 != 0)) {
         snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel 4 needs FP32 storage and nx %% 4 == 0");
         lbm_destroy(c);

@@ -12,7 +12,7 @@ template <class Codec, int COLL, int TY>
 cudaError_t launch_step_t(const StepLaunch& c, const void* src, void* dst) {
     constexpr int TX = 32;
     const StepArgs& a = c.args;
-    if constexpr ((std::is_same_v<Codec, CodecF32> || std::is_same_v<Codec, CodecF64>) && TY == 8) {
+    if constexpr ((std::is_same_v<Codec, CodecF32> || std::is_same_v<Codec, CodecF64>) && TY >= 8) {
         if (c.kernel == 6) {
             dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + a.zchunk - 1) / a.zchunk);
             sc_step_mr_kernel<Codec, COLL, TX, TY><<<grid, TX * TY, 0, c.stream>>>(
@@ -20,7 +20,7 @@ cudaError_t launch_step_t(const StepLaunch& c, const void* src, void* dst) {
             return cudaGetLastError();
         }
     }
-    if (c.kernel == 6) return cudaErrorNotSupported;  // FP64 / FP32 on 32x8 tiles only
+    if (c.kernel == 6) return cudaErrorNotSupported;  // FP64 / FP32 on 32x8 or 32x16 tiles only
     if constexpr (std::is_same_v<Codec, CodecF32>) {
         if (c.kernel == 4) {
             sc_step_bulk_kernel<COLL, TY><<<c.grid, BulkLayout<TY>::NT + 32, BulkLayout<TY>::bytes, c.stream>>>(
