@@ -123,8 +123,8 @@ typedef struct {
                              order).  Bulk EoS P = rho cs2 + cs2 (G + G2) psi^2/2;
                              the split of G + G2 sets the surface tension.  Runs
                              kernel 6 (register-staged, two-cell psi halo, 32x8
-                             tiles) with FP64/FP32 storage; not available to
-                             batches or the adjoint.                               */
+                             tiles, or 32x16 when tile_y = 16) with FP64/FP32
+                             storage; not available to batches or the adjoint.     */
 } lbm_params;
 
 /* Fill *p with defaults: D3Q19, 32^3, G = -5.5, SRT tau = 1, psi exp, rho0 = 1,
