@@ -42,7 +42,7 @@ BYTES_PER_POP = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "f16l": 2, "bf16l": 2}
 EXTRA_BYTES_PER_CELL = {"f16l": 8, "bf16l": 8}
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_NAMES = {1: "sc_step_kernel", 2: "sc_step_async_kernel", 3: "sc_step_pipe_kernel", 4: "sc_step_bulk_kernel",
-                5: "sc_step_tma_kernel"}
+                5: "sc_step_tma_kernel", 6: "sc_step_mr_kernel"}
 
 
 def parse_args():
@@ -56,6 +56,9 @@ def parse_args():
     ap.add_argument("--R0", type=float, default=64.0)
     ap.add_argument("--kR0", type=float, default=0.7)
     ap.add_argument("--tau", type=float, default=1.0)
+    ap.add_argument("--G2", type=float, default=0.0,
+                    help="single form: second belt of the two-belt force (kernel 6); the first belt is then "
+                         "-5.5 - G2, so the bulk EoS stays that of G = -5.5")
     ap.add_argument("--mrt-rule", choices=["shear", "paper"], default="shear",
                     help="MRT rates: shear moments at 1/tau (shear) or also the energy moment (paper)")
     ap.add_argument("--zchunk", type=int, default=0)
@@ -99,7 +102,8 @@ def workload(args):
     forcing = "shift" if args.collision == "srt" else "guo"
     rl, rv = inputs.COEXISTENCE[(forcing, -5.5, 1.0)]
     rule = f" ({args.mrt_rule} rule)" if args.collision == "mrt" else ""
-    name = (f"ligament R0={args.R0:g} kR0={args.kR0:g} box {nx}x{ny}x{nz}, G=-5.5, "
+    gtxt = "G=-5.5" if args.G2 == 0 else f"G1={-5.5 - args.G2:g} G2={args.G2:g} (two-belt force)"
+    name = (f"ligament R0={args.R0:g} kR0={args.kR0:g} box {nx}x{ny}x{nz}, {gtxt}, "
             f"{args.collision.upper()}{rule} tau={args.tau:g}, {args.storage.upper()} populations, "
             f"5% cosine perturbation")
     return dict(nx=nx, ny=ny, nz=nz, rho_l=rl, rho_v=rv, name=name)
@@ -275,7 +279,8 @@ def run_ours(args):
     w = workload(args)
     nx, ny, nz = w["nx"], w["ny"], w["nz"]
     ncell = nx * ny * nz
-    L = lbm.Lattice(nx, ny, nz, G=-5.5, tau=args.tau, collision=args.collision, storage=args.storage,
+    L = lbm.Lattice(nx, ny, nz, G=-5.5 - args.G2, G2=args.G2, tau=args.tau, collision=args.collision,
+                    storage=args.storage,
                     rates=mrt_rates(args), zchunk=args.zchunk, tile_y=args.tile_y, kernel=args.kernel)
     L.init_ligament(args.R0, 0.05, w["rho_l"], w["rho_v"])
     L_info = L.kernel_config()
