@@ -406,7 +406,7 @@ def step_record():
     with open(path) as fh:
         rec = json.load(fh)
     h = hashlib.sha256()
-    for f in ("step_kernel.cuh", "codec.cuh", "lattice.cuh"):
+    for f in ("step_kernel.cuh", "codec.cuh", "lattice.cuh", "step_multirange.cuh", "e8.cuh"):
         with open(os.path.join(ROOT, "paper_1905_09554_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return rec if rec.get("kernel_sha256") == h.hexdigest() else None
