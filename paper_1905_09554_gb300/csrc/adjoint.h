@@ -13,12 +13,23 @@ struct AdjointArgs {
 };
 
 int adjoint_threads();
-// One reverse step: lam_out = (dS/df)^T lam_next at the forward state f, and
-// acc[0] += dJ/dG, acc[1] += dJ/dtau of this step.  psi (n), gF (3n) and
-// partials (2 * grid doubles) are scratch.
+// The adjoint field is kept as lam_a(x) + gr(x): the force's contribution to
+// dJ/drho is the same for every population, so it is stored once per cell
+// (gr, n values) instead of being added to the 19 populations.
+//
+// One reverse step: (lam_out, gr_out) = (dS/df)^T (lam_next + gr_next) at the
+// forward state f; this step's dJ/dG and dJ/dtau are added to the per-block
+// running sums in `partials` (2 * grid doubles, zeroed before the first
+// step), which adjoint_reduce adds into acc[0..1] once after the last step.
+// psi (n) and gF (3n) are scratch; acc is not touched here.
 cudaError_t adjoint_step(const AdjointArgs& a, bool f64, const void* f, void* psi, const void* lam_next,
-                         void* lam_out, void* gF, double* partials, double* acc, cudaStream_t st);
-cudaError_t adjoint_seed(const AdjointArgs& a, bool f64, const double* dJdrho, void* lam, cudaStream_t st);
-cudaError_t adjoint_rho0(const AdjointArgs& a, bool f64, const void* lam, double* out, cudaStream_t st);
+                         const void* gr_next, void* lam_out, void* gr_out, void* gF, double* partials, double* acc,
+                         cudaStream_t st);
+cudaError_t adjoint_reduce(const AdjointArgs& a, const double* partials, double* acc, cudaStream_t st);
+// lam_a = dJ/drho (every a), gr = 0.
+cudaError_t adjoint_seed(const AdjointArgs& a, bool f64, const double* dJdrho, void* lam, void* gr, cudaStream_t st);
+// dJ/drho0 = sum_a w_a lam_a + gr.
+cudaError_t adjoint_rho0(const AdjointArgs& a, bool f64, const void* lam, const void* gr, double* out,
+                         cudaStream_t st);
 
 }  // namespace lbm

@@ -78,16 +78,17 @@ __device__ __forceinline__ void block_sum2(double a, double b, double* out2) {
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        out2[0] = red[0][0];
-        out2[1] = red[1][0];
+    if (threadIdx.x == 0) {  // the block's running sums over the reverse steps
+        out2[0] += red[0][0];
+        out2[1] += red[1][0];
     }
 }
 
 template <class R>
 __global__ void __launch_bounds__(kThreads)
 adj_collide_kernel(const R* __restrict__ f, const R* __restrict__ psi, const R* __restrict__ lam_next,
-                   R* __restrict__ lam_out, R* __restrict__ gF, double* __restrict__ partials, AdjointArgs a) {
+                   const R* __restrict__ gr_next, R* __restrict__ lam_out, R* __restrict__ gF,
+                   double* __restrict__ partials, AdjointArgs a) {
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const long long n = a.n;
     const R G = R(a.G), tau = R(a.tau), omega = R(a.omega);
@@ -104,7 +105,7 @@ adj_collide_kernel(const R* __restrict__ f, const R* __restrict__ psi, const R* 
             jy += R(cy(q)) * fv[q];
             jz += R(cz(q)) * fv[q];
             const long long nb = shifted(c, cx(q), cy(q), cz(q), nx, ny, nz);
-            ls[q] = lam_next[q * n + nb];  // streaming adjoint: pull from x + c_q
+            ls[q] = lam_next[q * n + nb] + gr_next[nb];  // streaming adjoint: pull from x + c_q
             if constexpr (q != 0) {
                 const R pn = psi[nb];
                 sx += R(wq(q) * cx(q)) * pn;
@@ -154,7 +155,7 @@ adj_collide_kernel(const R* __restrict__ f, const R* __restrict__ psi, const R* 
 
 template <class R>
 __global__ void __launch_bounds__(kThreads)
-adj_force_kernel(const R* __restrict__ psi, const R* __restrict__ gF, R* __restrict__ lam, AdjointArgs a) {
+adj_force_kernel(const R* __restrict__ psi, const R* __restrict__ gF, R* __restrict__ gr, AdjointArgs a) {
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const long long n = a.n;
     const R G = R(a.G), rho0 = R(a.rho0);
@@ -175,19 +176,17 @@ adj_force_kernel(const R* __restrict__ psi, const R* __restrict__ gF, R* __restr
         });
         term += sx * gF[i] + sy * gF[n + i] + sz * gF[2 * n + i];
         const R ps = psi[i];
-        const R g_rho = -G * term * (R(1) - ps / rho0);
-        static_for<0, Q>([&](auto qc) {
-            constexpr int q = decltype(qc)::value;
-            lam[q * n + i] += g_rho;
-        });
+        // the same for every population: stored once, added where it is read
+        gr[i] = -G * term * (R(1) - ps / rho0);
     }
 }
 
-// lam_a(x, T) = dJ/drho(x) for every a (rho = sum_a f_a).
+// lam_a(x, T) = dJ/drho(x) for every a (rho = sum_a f_a); no force term yet.
 template <class R>
-__global__ void adj_seed_kernel(const double* __restrict__ g, R* __restrict__ lam, long long n) {
+__global__ void adj_seed_kernel(const double* __restrict__ g, R* __restrict__ lam, R* __restrict__ gr, long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const R v = R(g[i]);
+        gr[i] = R(0);
         static_for<0, Q>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
             lam[q * n + i] = v;
@@ -195,11 +194,13 @@ __global__ void adj_seed_kernel(const double* __restrict__ g, R* __restrict__ la
     }
 }
 
-// f_a(x, 0) = w_a rho0(x): dJ/drho0(x) = sum_a w_a lam_a(x, 0).
+// f_a(x, 0) = w_a rho0(x): dJ/drho0(x) = sum_a w_a lam_a(x, 0), with
+// lam_a = stored part + force term gr (sum_a w_a = 1).
 template <class R>
-__global__ void adj_rho0_kernel(const R* __restrict__ lam, double* __restrict__ out, long long n) {
+__global__ void adj_rho0_kernel(const R* __restrict__ lam, const R* __restrict__ gr, double* __restrict__ out,
+                                long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        double s = 0.0;
+        double s = double(gr[i]);
         static_for<0, Q>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
             s += wq(q) * double(lam[q * n + i]);
@@ -208,53 +209,82 @@ __global__ void adj_rho0_kernel(const R* __restrict__ lam, double* __restrict__ 
     }
 }
 
-// Fixed-order sum of the per-block partials into acc[0..1].
-__global__ void adj_reduce_kernel(const double* __restrict__ partials, int nblocks, double* __restrict__ acc) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        double g = 0.0, t = 0.0;
-        for (int b = 0; b < nblocks; ++b) {
-            g += partials[2 * b];
-            t += partials[2 * b + 1];
+// Fixed-order sum of the per-block partials into acc[0..1]: each of 256
+// threads sums a strided subset in block order, then a fixed tree.
+__global__ void __launch_bounds__(kThreads) adj_reduce_kernel(const double* __restrict__ partials, int nblocks,
+                                                             double* __restrict__ acc) {
+    __shared__ double red[2][kThreads];
+    double g = 0.0, t = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += kThreads) {
+        g += partials[2 * b];
+        t += partials[2 * b + 1];
+    }
+    red[0][threadIdx.x] = g;
+    red[1][threadIdx.x] = t;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + s];
+            red[1][threadIdx.x] += red[1][threadIdx.x + s];
         }
-        acc[0] += g;
-        acc[1] += t;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        acc[0] += red[0][0];
+        acc[1] += red[1][0];
     }
 }
 
 template <class R>
-cudaError_t run_adjoint_step(const AdjointArgs& a, const void* f, void* psi, const void* lam_next, void* lam_out,
-                             void* gF, double* partials, double* acc, cudaStream_t st) {
+cudaError_t run_adjoint_step(const AdjointArgs& a, const void* f, void* psi, const void* lam_next,
+                             const void* gr_next, void* lam_out, void* gr_out, void* gF, double* partials,
+                             double* acc, cudaStream_t st) {
     const int grid = a.grid;
     adj_psi_kernel<R><<<grid, kThreads, 0, st>>>(static_cast<const R*>(f), static_cast<R*>(psi), a.n, R(a.rho0));
     adj_collide_kernel<R><<<grid, kThreads, 0, st>>>(static_cast<const R*>(f), static_cast<const R*>(psi),
-                                                     static_cast<const R*>(lam_next), static_cast<R*>(lam_out),
-                                                     static_cast<R*>(gF), partials, a);
+                                                     static_cast<const R*>(lam_next), static_cast<const R*>(gr_next),
+                                                     static_cast<R*>(lam_out), static_cast<R*>(gF), partials, a);
     adj_force_kernel<R><<<grid, kThreads, 0, st>>>(static_cast<const R*>(psi), static_cast<const R*>(gF),
-                                                   static_cast<R*>(lam_out), a);
-    adj_reduce_kernel<<<1, 32, 0, st>>>(partials, grid, acc);
+                                                   static_cast<R*>(gr_out), a);
+    (void)acc;  // the per-block sums stay in `partials` until adjoint_reduce
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t adjoint_step(const AdjointArgs& a, bool f64, const void* f, void* psi, const void* lam_next,
-                         void* lam_out, void* gF, double* partials, double* acc, cudaStream_t st) {
-    return f64 ? run_adjoint_step<double>(a, f, psi, lam_next, lam_out, gF, partials, acc, st)
-               : run_adjoint_step<float>(a, f, psi, lam_next, lam_out, gF, partials, acc, st);
+                         const void* gr_next, void* lam_out, void* gr_out, void* gF, double* partials, double* acc,
+                         cudaStream_t st) {
+    return f64 ? run_adjoint_step<double>(a, f, psi, lam_next, gr_next, lam_out, gr_out, gF, partials, acc, st)
+               : run_adjoint_step<float>(a, f, psi, lam_next, gr_next, lam_out, gr_out, gF, partials, acc, st);
 }
 
-cudaError_t adjoint_seed(const AdjointArgs& a, bool f64, const double* dJdrho, void* lam, cudaStream_t st) {
-    if (f64) adj_seed_kernel<double><<<a.grid, kThreads, 0, st>>>(dJdrho, static_cast<double*>(lam), a.n);
-    else adj_seed_kernel<float><<<a.grid, kThreads, 0, st>>>(dJdrho, static_cast<float*>(lam), a.n);
+cudaError_t adjoint_seed(const AdjointArgs& a, bool f64, const double* dJdrho, void* lam, void* gr, cudaStream_t st) {
+    if (f64)
+        adj_seed_kernel<double><<<a.grid, kThreads, 0, st>>>(dJdrho, static_cast<double*>(lam),
+                                                             static_cast<double*>(gr), a.n);
+    else
+        adj_seed_kernel<float><<<a.grid, kThreads, 0, st>>>(dJdrho, static_cast<float*>(lam), static_cast<float*>(gr),
+                                                            a.n);
     return cudaGetLastError();
 }
 
-cudaError_t adjoint_rho0(const AdjointArgs& a, bool f64, const void* lam, double* out, cudaStream_t st) {
-    if (f64) adj_rho0_kernel<double><<<a.grid, kThreads, 0, st>>>(static_cast<const double*>(lam), out, a.n);
-    else adj_rho0_kernel<float><<<a.grid, kThreads, 0, st>>>(static_cast<const float*>(lam), out, a.n);
+cudaError_t adjoint_rho0(const AdjointArgs& a, bool f64, const void* lam, const void* gr, double* out,
+                         cudaStream_t st) {
+    if (f64)
+        adj_rho0_kernel<double><<<a.grid, kThreads, 0, st>>>(static_cast<const double*>(lam),
+                                                             static_cast<const double*>(gr), out, a.n);
+    else
+        adj_rho0_kernel<float><<<a.grid, kThreads, 0, st>>>(static_cast<const float*>(lam),
+                                                            static_cast<const float*>(gr), out, a.n);
     return cudaGetLastError();
 }
 
 int adjoint_threads() { return kThreads; }
+
+cudaError_t adjoint_reduce(const AdjointArgs& a, const double* partials, double* acc, cudaStream_t st) {
+    adj_reduce_kernel<<<1, kThreads, 0, st>>>(partials, a.grid, acc);
+    return cudaGetLastError();
+}
 
 }  // namespace lbm

@@ -56,6 +56,7 @@ struct lbm_ctx {
         void* cp = nullptr;           // checkpoints, ncp states
         void* seg = nullptr;          // recomputed states of one segment, `every` states
         void* lam[2] = {nullptr, nullptr};
+        void* gr[2] = {nullptr, nullptr};  // the force term of lam, one value per cell
         void* psi = nullptr;
         void* gF = nullptr;
         double* partials = nullptr;   // 2 per block
@@ -752,6 +753,8 @@ void lbm_destroy(lbm_ctx* c) {
     cudaFree(c->adj.seg);
     cudaFree(c->adj.lam[0]);
     cudaFree(c->adj.lam[1]);
+    cudaFree(c->adj.gr[0]);
+    cudaFree(c->adj.gr[1]);
     cudaFree(c->adj.psi);
     cudaFree(c->adj.gF);
     cudaFree(c->adj.partials);
@@ -1422,6 +1425,10 @@ lbm_status lbm_adjoint_backward(lbm_ctx* c, const double* dJdrho, int in_on_devi
         st = adj_alloc(c, p, state);
         if (st != LBM_OK) return st;
     }
+    for (void** p : {&A.gr[0], &A.gr[1]}) {
+        st = adj_alloc(c, p, (size_t)c->n * c->elem);
+        if (st != LBM_OK) return st;
+    }
     if ((st = adj_alloc(c, &A.psi, (size_t)c->n * c->elem)) != LBM_OK) return st;
     if ((st = adj_alloc(c, &A.gF, 3 * (size_t)c->n * c->elem)) != LBM_OK) return st;
     if ((st = adj_alloc(c, reinterpret_cast<void**>(&A.partials), sizeof(double) * 2 * (size_t)a.grid)) != LBM_OK)
@@ -1436,7 +1443,8 @@ lbm_status lbm_adjoint_backward(lbm_ctx* c, const double* dJdrho, int in_on_devi
         g = A.io;
     }
     LBM_CUDA(c, cudaMemsetAsync(A.acc, 0, 2 * sizeof(double), c->stream));
-    LBM_CUDA(c, adjoint_seed(a, f64, g, A.lam[0], c->stream));
+    LBM_CUDA(c, cudaMemsetAsync(A.partials, 0, sizeof(double) * 2 * (size_t)a.grid, c->stream));
+    LBM_CUDA(c, adjoint_seed(a, f64, g, A.lam[0], A.gr[0], c->stream));
     int cur = 0;  // lam[cur] holds dJ/df(t+1)
     for (int k = A.ncp - 1; k >= 0; --k) {
         const long t0 = (long)k * A.every;
@@ -1450,15 +1458,16 @@ lbm_status lbm_adjoint_backward(lbm_ctx* c, const double* dJdrho, int in_on_devi
             if (e != cudaSuccess) return c->fail(LBM_ECUDA, "adjoint recompute: %s", cudaGetErrorString(e));
         }
         for (long t = t1 - 1; t >= t0; --t) {
-            cudaError_t e = adjoint_step(a, f64, seg + (size_t)(t - t0) * state, A.psi, A.lam[cur], A.lam[cur ^ 1],
-                                         A.gF, A.partials, A.acc, c->stream);
+            cudaError_t e = adjoint_step(a, f64, seg + (size_t)(t - t0) * state, A.psi, A.lam[cur], A.gr[cur],
+                                         A.lam[cur ^ 1], A.gr[cur ^ 1], A.gF, A.partials, A.acc, c->stream);
             if (e != cudaSuccess) return c->fail(LBM_ECUDA, "adjoint step: %s", cudaGetErrorString(e));
             cur ^= 1;
         }
     }
+    LBM_CUDA(c, adjoint_reduce(a, A.partials, A.acc, c->stream));
     if (dJdrho0) {
         double* out = out_on_device ? dJdrho0 : A.io;
-        LBM_CUDA(c, adjoint_rho0(a, f64, A.lam[cur], out, c->stream));
+        LBM_CUDA(c, adjoint_rho0(a, f64, A.lam[cur], A.gr[cur], out, c->stream));
         if (!out_on_device)
             LBM_CUDA(c, cudaMemcpyAsync(dJdrho0, A.io, sizeof(double) * (size_t)c->n, cudaMemcpyDeviceToHost, c->stream));
     }
