@@ -7,6 +7,7 @@ torch.autograd wrapper).
 * Against central finite differences of the GPU FP64 forward (h = 1e-4).
 * Checkpoint interval never changes a bit; the FP32 adjoint agrees with the
   FP64 one to FP32 accuracy.
+* A conserved objective (total mass) has the exact gradient 1, 0, 0.
 """
 
 import math
@@ -100,6 +101,21 @@ def test_adjoint_matches_central_differences_of_the_gpu_forward():
     fdT = (J(tau=TAU0 + h) - J(tau=TAU0 - h)) / (2 * h)
     assert abs(gG - fdG) <= 1e-6 * max(1e-8, abs(fdG)) + 1e-12
     assert abs(gT - fdT) <= 1e-6 * max(1e-8, abs(fdT)) + 1e-12
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 2e-5)])
+def test_conserved_objective_has_the_exact_gradient(storage, tol):
+    """J = total mass at step T is conserved by the step, so dJ/drho0 = 1 in
+    every cell and dJ/dG = dJ/dtau = 0, whatever the state: an exact answer
+    that tests the whole reverse pass (collision, streaming and force
+    adjoints and the parameter sums) with no reference to compare against."""
+    rho0 = small_case()
+    nz, ny, nx = rho0.shape
+    with lbm.Lattice(nx, ny, nz, G=G0, tau=TAU0, storage=storage) as L:
+        L.adjoint_forward(rho0, 40, 7)
+        g, dG, dtau = L.adjoint_backward(np.ones_like(rho0))
+    assert np.abs(g - 1.0).max() <= tol
+    assert abs(dG) <= tol * rho0.size and abs(dtau) <= tol * rho0.size, (dG, dtau)
 
 
 def test_checkpoint_interval_does_not_change_a_bit():
