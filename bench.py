@@ -662,7 +662,7 @@ def run_paper(args):
         with lbm.Lattice(nx, ny, nz, G=-5.3, tau=tau, collision=coll, storage="f32") as L:
             L.init_ligament(float(R0), eps, rl, rv, n_waves=2)
             ts, mins, drops = [], [], []
-            necks, amps, sil = [], [], {}
+            necks, amps, sil, vel = [], [], {}, {}
             t, broke_at = 0, None
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -678,7 +678,19 @@ def run_paper(args):
                         amps.append(dg.mode_amplitude(d["area_z"], n_waves=2))
                         for ts_star in (7, 8, 9):  # silhouettes R(z)/R0 at the first sample past t* (Fig. 5b)
                             if ts_star not in sil and t >= ts_star * tcap:
-                                sil[ts_star] = [round(float(v) / R0, 4) for v in dg.equivalent_radius(d["area_z"])]
+                                Rz = dg.equivalent_radius(d["area_z"])
+                                sil[ts_star] = [round(float(v) / R0, 4) for v in Rz]
+                                # velocity magnitude v* = |u_b| / (R0 / t_cap) (Fig. 7): where it peaks
+                                r_, u_ = L.moments()
+                                vs = np.sqrt((u_ ** 2).sum(axis=0)) / (R0 / tcap)
+                                vap = r_ < 0.5 * (rl + rv)
+                                zmax = int(np.unravel_index(int(np.argmax(vs)), vs.shape)[0])
+                                zneck = int(np.argmin(Rz))
+                                dz = min(abs(zmax - zneck), nz - abs(zmax - zneck))
+                                vel[ts_star] = {"v_max": float(vs.max()), "v_max_vapour": float(vs[vap].max()),
+                                                "v_max_liquid": float(vs[~vap].max()) if (~vap).any() else None,
+                                                "z_of_max_from_neck_over_R0": dz / R0}
+                                del r_, u_, vs, vap
                     if mins[-1] < 0.5 * (rl + rv):
                         broke_at = t
                 if broke_at is not None:
@@ -719,8 +731,10 @@ def run_paper(args):
                                    "neck_over_R0": [round(float(v), 4) for v in nk],
                                    "mode_amplitude_over_initial": [round(float(v) / a0, 4) for v in amps],
                                    "silhouettes_R_over_R0": {str(k): v for k, v in sil.items()},
+                                   "velocity_at_t_star": {str(k): v for k, v in vel.items()},
                                    "pinch_linear_fit": pinch}
-            print(json.dumps({"collision": coll, "R0": R0, "eps": eps, "pinch_linear_fit": pinch}), flush=True)
+            print(json.dumps({"collision": coll, "R0": R0, "eps": eps, "pinch_linear_fit": pinch,
+                              "velocity_at_t_star": {str(k): v for k, v in vel.items()}}), flush=True)
         print(json.dumps(cases[-1]), flush=True)
     print(json.dumps({"metric": "paper break-up experiment (Fig. 2b) at the paper's parameters",
                       "unit": "T_break / t_cap", "data": "synthetic", "cases": cases}), flush=True)
