@@ -159,8 +159,15 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.out.seek(0)
-        rows = [r.split(", ") for r in self.out.read().strip().splitlines() if r.count(",") >= 8]
+        text = self.out.read()
         os.unlink(self.out.name)
+        return self.parse(text)
+
+    @staticmethod
+    def parse(text):
+        """Median SM clock, maximum clock and the throttle reasons seen active
+        in nvidia-smi's csv,noheader,nounits lines of FIELDS."""
+        rows = [r.split(", ") for r in text.strip().splitlines() if r.count(",") >= 8]
         if not rows:
             return None
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]

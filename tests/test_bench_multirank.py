@@ -41,3 +41,34 @@ def test_single_process_is_the_identity():
     import bench
     assert bench.max_over_ranks(3.5) == 3.5
     assert bench.whole_job_mlups(37_683_200, 2000, 1000.0, 1) == pytest.approx(75366.4)
+
+
+def test_clock_parser_reads_only_active_reasons():
+    sys.path.insert(0, ROOT)
+    import bench
+    text = "\n".join([
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 950.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+    ])
+    got = bench.ClockSampler.parse(text)
+    assert got == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert bench.ClockSampler.parse("") is None
+
+
+def test_traffic_record_lookup_by_kernel_source_and_launch_shape():
+    """The committed ncu record is used only for the kernel sources it was
+    taken on and for a matching collision / storage / tau / launch shape."""
+    sys.path.insert(0, ROOT)
+    import argparse
+    import bench
+    rec = bench.step_record()
+    if rec is None:
+        pytest.skip("profiles/step_traffic.json was taken on other kernel sources")
+    args = argparse.Namespace(collision="srt", storage="f32", tau=1.0)
+    info = {"kernel": 3, "tile_y": 16, "zchunk": 32}
+    n = 37_683_200
+    per_cell = rec["bytes_per_cell"]["srt_f32_tau1_k3_ty16_zc32"]
+    assert 152.0 <= per_cell < 160.0
+    assert bench.load_traffic(args, n, info) == pytest.approx(per_cell * n)
+    assert bench.load_traffic(args, n, dict(info, zchunk=58)) is None
