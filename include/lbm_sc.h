@@ -166,7 +166,7 @@ lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f, int on_device);
 lbm_status lbm_get_populations(lbm_ctx *ctx, double *f, int on_device);
 
 /* Advance n >= 0 time steps (Eq. LBE): Shan-Chen force (Eq. SC_force with the
- * psi law), SRT with the shifted equilibrium velocity u' = u + tau F / rho
+ * psi law, plus the second belt when G2 != 0), SRT with the shifted equilibrium velocity u' = u + tau F / rho
  * (Eq. vel_shift) or MRT with Guo-like forcing at u_b = u + F/(2 rho)
  * (Eq. barycentric), then periodic streaming.  Enqueues n kernel launches. */
 lbm_status lbm_step(lbm_ctx *ctx, long n);
@@ -176,8 +176,8 @@ long lbm_time(const lbm_ctx *ctx);
 
 /* Macroscopic fields of the current state (Eq. momentum): rho and the
  * barycentric velocity u_b = (sum_a c_a f_a + F/2) / rho (Eq. barycentric),
- * reported for both operators.  Each output (host or device, float64,
- * nx*ny*nz) may be NULL to skip it. */
+ * reported for both operators (F includes the second belt when G2 != 0).
+ * Each output (host or device, float64, nx*ny*nz) may be NULL to skip it. */
 lbm_status lbm_moments(lbm_ctx *ctx, double *rho, double *ux, double *uy,
                        double *uz, int on_device);
 
@@ -221,8 +221,9 @@ lbm_status lbm_load(lbm_ctx *ctx, const char *path);
 long long lbm_device_bytes(const lbm_ctx *ctx);
 
 /* Launch configuration the context chose for the step kernel: variant
- * (1 register-staged, 2 cp.async-staged, 3 pipelined, 4 bulk-copy), tile height, z planes
- * per work item and grid size (blocks).  Any pointer may be NULL. */
+ * (1 register-staged, 2 cp.async-staged, 3 pipelined, 4 bulk-copy, 5 tensor
+ * copy, 6 two-belt force), tile height, z planes per work item and grid size
+ * (blocks).  Any pointer may be NULL. */
 lbm_status lbm_kernel_config(const lbm_ctx *ctx, int *kernel, int *tile_y,
                              int *zchunk, int *grid);
 
@@ -241,7 +242,7 @@ long long lbm_params_sizeof(void);
  * n >= 1 steps and keep every `every`-th state (t = 0, every, 2 every, ...) as
  * a checkpoint in device memory owned by the context; the state ends at
  * t = n.  Checkpoint memory: ceil(n/every) + every states.  Collision must be
- * LBM_SRT_SHIFT (else LBM_EUNSUPPORTED). */
+ * LBM_SRT_SHIFT and G2 zero (else LBM_EUNSUPPORTED). */
 lbm_status lbm_adjoint_forward(lbm_ctx *ctx, const double *rho0, int on_device,
                                long n, int every);
 
