@@ -639,7 +639,7 @@ def run_paper(args):
     import numpy as np
     import torch
 
-    from paper_1905_09554_gb300 import diagnostics as dg
+    from paper_1905_09554_gb300 import experiments as ex
     from paper_1905_09554_gb300 import lbm
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     gold = os.path.join(ROOT, "tests", "golden")
@@ -668,80 +668,26 @@ def run_paper(args):
         every = max(1, int(tcap / 40))
         with lbm.Lattice(nx, ny, nz, G=-5.3, tau=tau, collision=coll, storage="f32") as L:
             L.init_ligament(float(R0), eps, rl, rv, n_waves=2)
-            ts, mins, drops = [], [], []
-            necks, amps, sil, vel = [], [], {}, {}
-            t, broke_at = 0, None
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            while t <= 30 * tcap:
-                d = L.diag(rl, rv, raise_nonfinite=False)
-                if d["status"] != 0:
-                    break
-                if broke_at is None:
-                    ts.append(t)
-                    mins.append(float(d["maxrho_z"].min()))
-                    if args.series:
-                        necks.append(dg.neck_radius(d["area_z"]) / R0)
-                        amps.append(dg.mode_amplitude(d["area_z"], n_waves=2))
-                        for ts_star in (7, 8, 9):  # silhouettes R(z)/R0 at the first sample past t* (Fig. 5b)
-                            if ts_star not in sil and t >= ts_star * tcap:
-                                Rz = dg.equivalent_radius(d["area_z"])
-                                sil[ts_star] = [round(float(v) / R0, 4) for v in Rz]
-                                # velocity magnitude v* = |u_b| / (R0 / t_cap) (Fig. 7): where it peaks
-                                r_, u_ = L.moments()
-                                vs = np.sqrt((u_ ** 2).sum(axis=0)) / (R0 / tcap)
-                                vap = r_ < 0.5 * (rl + rv)
-                                zmax = int(np.unravel_index(int(np.argmax(vs)), vs.shape)[0])
-                                zneck = int(np.argmin(Rz))
-                                dz = min(abs(zmax - zneck), nz - abs(zmax - zneck))
-                                vel[ts_star] = {"v_max": float(vs.max()), "v_max_vapour": float(vs[vap].max()),
-                                                "v_max_liquid": float(vs[~vap].max()) if (~vap).any() else None,
-                                                "z_of_max_from_neck_over_R0": dz / R0}
-                                del r_, u_, vs, vap
-                    if mins[-1] < 0.5 * (rl + rv):
-                        broke_at = t
-                if broke_at is not None:
-                    # drops on the axis for one t_cap after the pinch-off: the
-                    # paper counts satellites that live about a capillary time
-                    drops.append(dg.count_drops(d["maxrho_z"], rl, rv))
-                    if t >= broke_at + tcap:
-                        break
-                L.step(every)
-                t += every
+            res = ex.breakup_run(L, R0, tcap, rl, rv, every, series=args.series)
             torch.cuda.synchronize()
             wall = time.perf_counter() - t0
             cfg = L.kernel_config()
-        tb = dg.breakup_time(ts, mins, rl, rv)
+        tb = res["T_break_over_tcap"]
         cases.append({"collision": coll, "R0": R0, "eps": eps, "box": [nx, ny, nz], "tau": tau, "t_cap": tcap,
-                      "rho_l": rl, "rho_v": rv, "steps": t, "diag_every": every,
-                      "drops_max": max(drops) if drops else None, "drops_final": drops[-1] if drops else None,
-                      "satellites": max(0, drops[-1] - 2) if drops else None,
-                      "satellites_transient": max(0, max(drops) - 2) if drops else None, "paper_satellites": fig_sat,
-                      "T_break_over_tcap": tb / tcap if tb is not None else None,
+                      "rho_l": rl, "rho_v": rv, "steps": res["steps"], "diag_every": every,
+                      "drops_max": res["drops_max"], "drops_final": res["drops_final"],
+                      "satellites": res["satellites"], "satellites_transient": res["satellites_transient"],
+                      "paper_satellites": fig_sat, "T_break_over_tcap": tb,
                       "paper_T_break": fig_t, "lsa_T_break": lsa_t,
-                      "rel_diff": (tb / tcap - fig_t) / fig_t if tb is not None and fig_t else None,
-                      "wall_s": wall, "glups": nx * ny * nz * t / wall / 1e9, "kernel": cfg})
-        if args.series and ts:
-            tt = np.asarray(ts[:len(necks)], dtype=float) / tcap
-            nk = np.asarray(necks)
-            a0 = amps[0] if amps and amps[0] != 0 else 1.0
-            # final pinch (Fig. 6): R_min / R0 against t* where it falls from 0.3 to 0.05
-            sel = (nk <= 0.3) & (nk >= 0.05)
-            pinch = None
-            if sel.sum() >= 3:
-                sl, ic = np.polyfit(tt[sel], nk[sel], 1)
-                fit = sl * tt[sel] + ic
-                ss = float(((nk[sel] - nk[sel].mean()) ** 2).sum())
-                pinch = {"slope_R0_per_tcap": float(sl), "points": int(sel.sum()),
-                         "r2": 1.0 - float(((nk[sel] - fit) ** 2).sum()) / ss if ss > 0 else 1.0}
-            cases[-1]["series"] = {"t_star": [round(float(v), 4) for v in tt],
-                                   "neck_over_R0": [round(float(v), 4) for v in nk],
-                                   "mode_amplitude_over_initial": [round(float(v) / a0, 4) for v in amps],
-                                   "silhouettes_R_over_R0": {str(k): v for k, v in sil.items()},
-                                   "velocity_at_t_star": {str(k): v for k, v in vel.items()},
-                                   "pinch_linear_fit": pinch}
-            print(json.dumps({"collision": coll, "R0": R0, "eps": eps, "pinch_linear_fit": pinch,
-                              "velocity_at_t_star": {str(k): v for k, v in vel.items()}}), flush=True)
+                      "rel_diff": (tb - fig_t) / fig_t if tb is not None and fig_t else None,
+                      "wall_s": wall, "glups": nx * ny * nz * res["steps"] / wall / 1e9, "kernel": cfg})
+        if "series" in res:
+            cases[-1]["series"] = res["series"]
+            print(json.dumps({"collision": coll, "R0": R0, "eps": eps,
+                              "pinch_linear_fit": res["series"]["pinch_linear_fit"],
+                              "velocity_at_t_star": res["series"]["velocity_at_t_star"]}), flush=True)
         print(json.dumps(cases[-1]), flush=True)
     print(json.dumps({"metric": "paper break-up experiment (Fig. 2b) at the paper's parameters",
                       "unit": "T_break / t_cap", "data": "synthetic", "cases": cases}), flush=True)
@@ -749,8 +695,8 @@ def run_paper(args):
 
 def run_calibrate(args):
     """The calibration of Sec. 3 at G0 = -5.3, Oh = 0.1, measured with the GPU
-    step: SRT iterates tau -> (Laplace test on droplets of radius 12, 16, 20
-    in an 80^3 box, flat slab) -> the tau that meets Oh, from --tau0 until
+    step: SRT iterates tau -> (Laplace test on droplets of radius 16, 20, 24
+    in boxes of 4 R, flat slab) -> the tau that meets Oh, from --tau0 until
     two consecutive sigma agree to --cal-tol; MRT (rates of Sec. 2) takes one
     pass at Table 2's tau.  Reports tau, sigma, rho_l, rho_v and t_cap beside
     Tables 1 and 2."""

@@ -1,0 +1,107 @@
+"""The paper's break-up run (Secs. 3-4) as a driver over a lattice: step to
+the pinch-off while sampling the diagnostics, count the drops for a
+capillary time after it, and optionally record the series behind Figs. 5-7.
+
+Works with any object that has the `Lattice` methods it uses (`diag`,
+`step`, `moments`); the arithmetic of the step is the library's.  Host-side
+analysis only (numpy), built on `diagnostics`.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+from . import diagnostics as dg
+
+SNAPSHOT_T_STAR = (7, 8, 9)  # silhouettes and velocity (Figs. 5b and 7)
+
+
+def pinch_linear_fit(t_star, neck_over_R0, hi=0.3, lo=0.05, min_points=3):
+    """Least-squares line of R_min/R0 against t* over the samples with
+    lo <= R_min/R0 <= hi (the final pinch, Fig. 6): slope, points, r^2."""
+    tt = np.asarray(t_star, dtype=float)
+    nk = np.asarray(neck_over_R0, dtype=float)
+    sel = (nk <= hi) & (nk >= lo)
+    if sel.sum() < min_points:
+        return None
+    sl, ic = np.polyfit(tt[sel], nk[sel], 1)
+    fit = sl * tt[sel] + ic
+    ss = float(((nk[sel] - nk[sel].mean()) ** 2).sum())
+    return {"slope_R0_per_tcap": float(sl), "points": int(sel.sum()),
+            "r2": 1.0 - float(((nk[sel] - fit) ** 2).sum()) / ss if ss > 0 else 1.0}
+
+
+def velocity_snapshot(rho, u, rho_l, rho_v, R0, tcap, Rz):
+    """Where v* = |u_b| / (R0 / t_cap) peaks (Fig. 7): overall, in the vapour
+    (rho below the mid density) and in the liquid, and the distance in z of
+    the peak from the neck slice, in units of R0."""
+    nz = rho.shape[0]
+    vs = np.sqrt((u ** 2).sum(axis=0)) / (R0 / tcap)
+    vap = rho < 0.5 * (rho_l + rho_v)
+    zmax = int(np.unravel_index(int(np.argmax(vs)), vs.shape)[0])
+    zneck = int(np.argmin(Rz))
+    dz = min(abs(zmax - zneck), nz - abs(zmax - zneck))
+    return {"v_max": float(vs.max()),
+            "v_max_vapour": float(vs[vap].max()) if vap.any() else None,
+            "v_max_liquid": float(vs[~vap].max()) if (~vap).any() else None,
+            "z_of_max_from_neck_over_R0": dz / R0}
+
+
+def breakup_run(L, R0, tcap, rho_l, rho_v, every, series=False, max_tcap=30.0, after_tcap=1.0, n_waves=2):
+    """Step `L` (already initialised) in strides of `every` steps, sampling
+    `L.diag` before each stride, until some z slice holds no liquid (the
+    break-up), then for `after_tcap` capillary times more while counting the
+    drops on the axis.  Stops early on a non-finite state or after
+    `max_tcap` capillary times.
+
+    Returns a dict: steps, t_break (steps, interpolated) and
+    T_break_over_tcap (None if no break-up), drops_max / drops_final and the
+    satellites (drops beyond the n_waves main ones at the end / at most), and
+    with `series` the neck-radius and mode-amplitude series, the silhouettes
+    and velocity snapshots at t* = 7, 8, 9 (first sample past each) and the
+    linear fit of the final pinch."""
+    ts, mins, drops = [], [], []
+    necks, amps, sil, vel = [], [], {}, {}
+    t, broke_at, status = 0, None, 0
+    while t <= max_tcap * tcap:
+        d = L.diag(rho_l, rho_v, raise_nonfinite=False)
+        status = d["status"]
+        if status != 0:
+            break
+        if broke_at is None:
+            ts.append(t)
+            mins.append(float(d["maxrho_z"].min()))
+            if series:
+                necks.append(dg.neck_radius(d["area_z"]) / R0)
+                amps.append(dg.mode_amplitude(d["area_z"], n_waves=n_waves))
+                for ts_star in SNAPSHOT_T_STAR:
+                    if ts_star not in sil and t >= ts_star * tcap:
+                        Rz = dg.equivalent_radius(d["area_z"])
+                        sil[ts_star] = [round(float(v) / R0, 4) for v in Rz]
+                        rho, u = L.moments()
+                        vel[ts_star] = velocity_snapshot(rho, u, rho_l, rho_v, R0, tcap, Rz)
+                        del rho, u
+            if mins[-1] < 0.5 * (rho_l + rho_v):
+                broke_at = t
+        if broke_at is not None:
+            drops.append(dg.count_drops(d["maxrho_z"], rho_l, rho_v))
+            if t >= broke_at + after_tcap * tcap:
+                break
+        L.step(every)
+        t += every
+    tb = dg.breakup_time(ts, mins, rho_l, rho_v)
+    out = {"steps": t, "status": status, "t_break": tb,
+           "T_break_over_tcap": tb / tcap if tb is not None else None,
+           "drops_max": max(drops) if drops else None, "drops_final": drops[-1] if drops else None,
+           "satellites": max(0, drops[-1] - n_waves) if drops else None,
+           "satellites_transient": max(0, max(drops) - n_waves) if drops else None}
+    if series and ts:
+        tt = np.asarray(ts[:len(necks)], dtype=float) / tcap
+        a0 = amps[0] if amps and amps[0] != 0 else 1.0
+        out["series"] = {"t_star": [round(float(v), 4) for v in tt],
+                         "neck_over_R0": [round(float(v), 4) for v in necks],
+                         "mode_amplitude_over_initial": [round(float(v) / a0, 4) for v in amps],
+                         "silhouettes_R_over_R0": {str(k): v for k, v in sil.items()},
+                         "velocity_at_t_star": {str(k): v for k, v in vel.items()},
+                         "pinch_linear_fit": pinch_linear_fit(tt, necks)}
+    return out
