@@ -247,6 +247,40 @@ def test_shear_wave_decays_with_the_lattice_viscosity(coll, tau):
     assert abs(-slope / (k * k) / nu - 1.0) < 2e-3
 
 
+# -------------------------------------------------------------- sound speed
+@pytest.mark.parametrize("G,coll,tau", [(0.0, "srt", 0.8), (-2.0, "srt", 0.8), (-2.0, "mrt", 0.8)])
+def test_sound_speed_follows_the_equation_of_state(G, coll, tau):
+    """A small standing density wave in a uniform single-phase fluid
+    oscillates at omega = c k with c^2 = dP/drho of Eq. EOS_SC,
+    cs2 (1 + G psi psi'): ideal-gas cs2 = 1/3 at G = 0, about half of it at
+    G = -2, rho = 1.  Pins the force's normalisation and the equilibrium's
+    pressure term through the dynamics (lattice dispersion is O(k^2))."""
+    from scipy.optimize import curve_fit
+
+    L, rho0, steps = 128, 1.0, 700
+    k = 2 * math.pi / L
+    x = np.arange(L)
+    rho = (rho0 + 1e-5 * np.cos(k * x))[None, None, :]
+    p = o.Params(G=G, tau=tau, collision=coll)
+    f = o.init_populations(rho)
+    amp = []
+    for _ in range(steps):
+        amp.append(2.0 / L * ((f.sum(0)[0, 0, :] - rho0) * np.cos(k * x)).sum())
+        f = o.step(f, p)
+    psi, dpsi = 1 - math.exp(-rho0), math.exp(-rho0)
+    c2 = (1 + G * psi * dpsi) / 3.0
+    w0 = math.sqrt(c2) * k
+
+    def damped(t, A, w, g, ph):
+        return A * np.cos(w * t + ph) * np.exp(-g * t)
+
+    popt, _ = curve_fit(damped, np.arange(steps), np.array(amp), p0=[1e-5, w0, 1e-3, 0.0])
+    assert abs(popt[1] / w0 - 1) < 1e-3, (popt[1], w0)
+    # and the wrong EoS (the ideal gas) is far off when G != 0
+    if G != 0:
+        assert abs(popt[1] / (k / math.sqrt(3)) - 1) > 0.2
+
+
 # -------------------------------------------------------- flat interfaces
 def flat_interface(G, coll, tau, rl, rv, n=32, max_steps=40000, s=None):
     """Run a flat liquid slab (fields vary along z only) to steady state;
