@@ -86,3 +86,30 @@ def test_long_wave_expansion_same_eos_different_third_order(L):
     # the O(k^3) difference between the belts is resolved
     d = mr.belt_sum(psi, mr.E8, mr.P8 / 3.0)[0, 0, 0] - mr.belt_sum(psi, o.C, o.W)[0, 0, 0]
     assert np.abs(d).max() > 0.5 * (e4_8 - e4_19) * k ** 3 / 6.0
+
+
+def test_two_belt_sound_speed_follows_g1_plus_g2():
+    """A standing density wave oscillates at c k with c^2 = cs2 (1 + (G1 + G2)
+    psi psi'): the split G1 = -3, G2 = +1 sounds like the single belt at
+    G = -2 (the bulk EoS depends on G1 + G2 only)."""
+    from scipy.optimize import curve_fit
+
+    L, rho0, steps = 128, 1.0, 700
+    k = 2 * math.pi / L
+    x = np.arange(L)
+    p = o.Params(G=-3.0, tau=0.8, collision="srt")
+    f = o.init_populations((rho0 + 1e-5 * np.cos(k * x))[None, None, :])
+    amp = []
+    for _ in range(steps):
+        amp.append(2.0 / L * ((f.sum(0)[0, 0, :] - rho0) * np.cos(k * x)).sum())
+        f = o.stream(mr.collide(f, p, 1.0))
+    psi, dpsi = 1 - math.exp(-rho0), math.exp(-rho0)
+    w0 = math.sqrt((1 + (-3.0 + 1.0) * psi * dpsi) / 3.0) * k
+
+    def damped(t, A, w, g, ph):
+        return A * np.cos(w * t + ph) * np.exp(-g * t)
+
+    popt, _ = curve_fit(damped, np.arange(steps), np.array(amp), p0=[1e-5, w0, 1e-3, 0.0])
+    assert abs(popt[1] / w0 - 1) < 2e-3, (popt[1], w0)
+    w_g1_only = math.sqrt((1 - 3.0 * psi * dpsi) / 3.0) * k
+    assert abs(popt[1] / w_g1_only - 1) > 0.1
