@@ -281,6 +281,39 @@ def test_sound_speed_follows_the_equation_of_state(G, coll, tau):
         assert abs(popt[1] / (k / math.sqrt(3)) - 1) > 0.2
 
 
+@pytest.mark.parametrize("tau", [0.7, 0.9])
+@pytest.mark.parametrize("op", ["srt", "mrt-paper", "mrt-shear"])
+def test_sound_attenuation_follows_shear_and_bulk_viscosity(op, tau):
+    """A standing sound wave decays as exp(-Gamma t) with
+    Gamma = k^2 (2 nu / 3 + zeta / 2), nu = cs2 (tau - 1/2) and the bulk
+    viscosity zeta = (2/9) (1/s_e - 1/2) of the energy-moment rate s_e of the
+    D3Q19 basis.  SRT and the paper's MRT rule (s_e = 1/tau) give
+    zeta = 2 nu / 3, i.e. Gamma = nu k^2; the shear rule (s_e = 1) gives
+    zeta = 1/9.  Pins the e row of the basis and the rate assignment."""
+    from scipy.optimize import curve_fit
+
+    L, rho0, steps = 128, 1.0, 700
+    k = 2 * math.pi / L
+    x = np.arange(L)
+    coll = "srt" if op == "srt" else "mrt"
+    s = None if op == "srt" else o.mrt_rates(tau, rule=op.split("-")[1])
+    p = o.Params(G=0.0, tau=tau, collision=coll, s=s)
+    f = o.init_populations((rho0 + 1e-5 * np.cos(k * x))[None, None, :])
+    amp = []
+    for _ in range(steps):
+        amp.append(2.0 / L * ((f.sum(0)[0, 0, :] - rho0) * np.cos(k * x)).sum())
+        f = o.step(f, p)
+
+    def damped(t, A, w, g, ph):
+        return A * np.cos(w * t + ph) * np.exp(-g * t)
+
+    popt, _ = curve_fit(damped, np.arange(steps), np.array(amp), p0=[1e-5, k / math.sqrt(3), 1e-3, 0.0])
+    nu = (tau - 0.5) / 3.0
+    s_e = 1.0 / tau if op != "mrt-shear" else 1.0
+    zeta = 2.0 / 9.0 * (1.0 / s_e - 0.5)
+    assert abs(popt[2] / (k * k * (2 * nu / 3 + zeta / 2)) - 1) < 1e-3, (op, tau, popt[2] / k ** 2)
+
+
 # -------------------------------------------------------- flat interfaces
 def flat_interface(G, coll, tau, rl, rv, n=32, max_steps=40000, s=None):
     """Run a flat liquid slab (fields vary along z only) to steady state;
