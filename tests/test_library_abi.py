@@ -88,6 +88,23 @@ def test_local_reference_storage_runs_kernels_1_and_3_only(lib):
             assert "kernel 1 or 3" in lbm.lbm_last_error(None)
 
 
+def test_two_belt_force_parameters_are_validated_before_device_work(lib):
+    cases = [
+        dict(G2=float("nan")),
+        dict(G2=-1.0, storage=lbm.LBM_F16_DEV),
+        dict(G2=-1.0, kernel=3),
+        dict(G2=-1.0, tile_y=4),
+        dict(G2=0.0, kernel=6),
+    ]
+    for case in cases:
+        p = lbm.lbm_params_default()
+        for k, v in case.items():
+            setattr(p, k, v)
+        st, ctx = lbm.lbm_create(p)
+        assert st == lbm.LBM_EINVAL and not ctx.value, case
+        assert "G2" in lbm.lbm_last_error(None) or "two-belt" in lbm.lbm_last_error(None), case
+
+
 def test_noalloc_diagnostics_reject_local_reference_storage(lib):
     """The local formats need a context's density field; refused before any
     device work."""
