@@ -3,6 +3,7 @@ declares; host-side validation and tables work without a GPU.  CPU only: no
 call here launches a kernel."""
 
 import ctypes
+import os
 
 import numpy as np
 import pytest
@@ -130,3 +131,39 @@ def test_noalloc_diagnostics_reject_boxes_beyond_the_static_scratch(lib):
     st = lbm.lbm_diag_noalloc(None, lbm.LBM_F32, 4, 4, 8, 1.0, 1.0, 2.3, 0.1,
                               None, None, None, None, 0, None)
     assert st == lbm.LBM_EINVAL
+
+
+def test_header_is_plain_c_and_links_from_c(lib, tmp_path):
+    """include/lbm_sc.h compiles as C99 and a C program links against the
+    library: the struct layout seen by C matches the library's, and a
+    validation failure comes back as a status and a message (no GPU work)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include <string.h>
+#include "lbm_sc.h"
+int main(void) {
+    lbm_params p;
+    lbm_ctx *ctx = (lbm_ctx *)1;
+    lbm_params_default(&p);
+    if ((long long)sizeof(lbm_params) != lbm_params_sizeof()) return 2;
+    if (p.nx != 32 || p.storage != LBM_F32 || p.G2 != 0.0) return 3;
+    p.tau = 0.25;
+    if (lbm_create(&p, &ctx) != LBM_EINVAL || ctx != NULL) return 4;
+    if (strstr(lbm_last_error(NULL), "tau") == NULL) return 5;
+    puts("ok");
+    return 0;
+}
+""")
+    pkg = os.path.dirname(lbm.LIB_PATH)
+    exe = tmp_path / "abi"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.dirname(lbm.HEADER), str(src), "-o", str(exe),
+                    "-L", pkg, "-llbm_sc", f"-Wl,-rpath,{pkg}"], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", (out.returncode, out.stdout, out.stderr)
