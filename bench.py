@@ -206,6 +206,29 @@ def oracle_mlups(w, args, slab, min_seconds, max_steps):
     return cells * steps / dt / 1e6, max(1, round(cpu / dt)), desc, steps
 
 
+def c_reference_mlups(w, args, slab, steps):
+    """The OpenMP C reference (oracle/c/lbm_ref.c, SRT only) on the same slab,
+    all host threads: (MLUPS, threads, description), or None where it is not
+    available (no C compiler, MRT, G2 != 0)."""
+    if args.collision != "srt" or getattr(args, "G2", 0.0) != 0.0:
+        return None
+    try:
+        from oracle import c_ref, lbm_oracle as o
+        from paper_1905_09554_gb300 import inputs
+        rho = inputs.ligament_density(w["nx"], w["ny"], slab, args.R0, 0.05, w["rho_l"], w["rho_v"])
+        f = o.init_populations(rho)
+        c_ref.run_srt(f, 1, -5.5, args.tau)  # build, load, warm up
+        t0 = time.perf_counter()
+        c_ref.run_srt(f, steps, -5.5, args.tau)
+        dt = time.perf_counter() - t0
+        n = c_ref.threads()
+    except Exception:  # noqa: BLE001 - optional: no compiler or OpenMP on this host
+        return None
+    desc = (f"FP64 C reference with OpenMP ({n} threads), {steps} SRT steps of the same "
+            f"{w['nx']}x{w['ny']}x{slab} slab")
+    return rho.size * steps / dt / 1e6, n, desc
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -383,6 +406,10 @@ def run_ours(args):
     if not args.no_cpu_baseline and world == 1:
         mlups, cores, desc, _ = oracle_mlups(w, args, slab=16, min_seconds=10.0, max_steps=20)
         cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": desc}
+        c_res = c_reference_mlups(w, args, slab=16, steps=40)
+        if c_res is not None:  # the same method in plain C on every host thread
+            cpu["openmp_c_reference"] = {"value": c_res[0], "unit": "MLUPS", "threads": c_res[1],
+                                         "sample": c_res[2]}
 
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
