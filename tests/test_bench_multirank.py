@@ -72,3 +72,28 @@ def test_traffic_record_lookup_by_kernel_source_and_launch_shape():
     assert 152.0 <= per_cell < 160.0
     assert bench.load_traffic(args, n, info) == pytest.approx(per_cell * n)
     assert bench.load_traffic(args, n, dict(info, zchunk=58)) is None
+
+
+def test_reference_arm_prints_the_contract_line_and_other_ranks_stay_silent():
+    """`bench.py --impl reference` times the oracle on the host and prints one
+    JSON line with the contract's keys; a rank other than 0 prints nothing."""
+    import json
+    import subprocess
+
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1", "--warmup", "0"]
+    env = dict(os.environ, RANK="0")
+    out = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["unit"] == "MLUPS" and d["value"] > 0 and d["higher_is_better"]
+    assert "workload" in d["config"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert set(d["e2e"]) == {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
+    out1 = subprocess.run(cmd, capture_output=True, text=True, env=dict(os.environ, RANK="1"), timeout=600,
+                          cwd=ROOT)
+    assert out1.returncode == 0 and out1.stdout.strip() == ""
