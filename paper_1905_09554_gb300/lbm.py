@@ -277,6 +277,26 @@ def _host_ptr(a: np.ndarray):
     return a.ctypes.data_as(_P)
 
 
+def _host_array(a, numel, what):
+    """float64 C-contiguous copy (or view) of a host array of numel values."""
+    arr = np.ascontiguousarray(a, dtype=np.float64)
+    if arr.size != numel:
+        raise ValueError(f"{what}: expected {numel} values, got {arr.size}")
+    return arr
+
+
+def _device_tensor(t, numel, what):
+    """Check a CUDA float64 contiguous tensor of numel values (the library
+    reads or writes it in place, so no conversion is made)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what}: expected a numpy array or a CUDA tensor")
+    if t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != numel:
+        raise ValueError(f"{what}: need a contiguous float64 CUDA tensor of {numel} values "
+                         f"(got {t.dtype}, contiguous={t.is_contiguous()}, {t.numel()} values)")
+    return t.data_ptr()
+
+
 def _params(G=-5.5, tau=1.0, collision="srt", rates=None, storage="f32", rho0=1.0, rho_ref=1.0,
             dev_scale=1.0, zchunk=0, tile_y=0, kernel=0):
     p = lbm_params_default()
@@ -378,28 +398,23 @@ class Lattice:
     def set_density(self, rho):
         """rho: numpy float64 (nz, ny, nx) or a contiguous float64 CUDA tensor."""
         if isinstance(rho, np.ndarray):
-            a = np.ascontiguousarray(rho, dtype=np.float64)
-            assert a.size == self.n
+            a = _host_array(rho, self.n, "set_density")
             self._check(lbm_set_density(self.ctx, _host_ptr(a), 0))
         else:
-            assert rho.is_cuda and rho.numel() == self.n and rho.is_contiguous()
-            self._check(lbm_set_density(self.ctx, rho.data_ptr(), 1))
+            self._check(lbm_set_density(self.ctx, _device_tensor(rho, self.n, "set_density"), 1))
 
     def set_populations(self, f):
         if isinstance(f, np.ndarray):
-            a = np.ascontiguousarray(f, dtype=np.float64)
-            assert a.size == 19 * self.n
+            a = _host_array(f, 19 * self.n, "set_populations")
             self._check(lbm_set_populations(self.ctx, _host_ptr(a), 0))
         else:
-            assert f.is_cuda and f.numel() == 19 * self.n and f.is_contiguous()
-            self._check(lbm_set_populations(self.ctx, f.data_ptr(), 1))
+            self._check(lbm_set_populations(self.ctx, _device_tensor(f, 19 * self.n, "set_populations"), 1))
 
     def get_populations(self, out=None):
         """float64 populations (19, nz, ny, nx), library velocity order; into
         a CUDA tensor ``out`` if given, else a new numpy array."""
         if out is not None:
-            assert out.is_cuda and out.numel() == 19 * self.n
-            self._check(lbm_get_populations(self.ctx, out.data_ptr(), 1))
+            self._check(lbm_get_populations(self.ctx, _device_tensor(out, 19 * self.n, "get_populations"), 1))
             return out
         a = np.empty((19,) + self.shape)
         self._check(lbm_get_populations(self.ctx, _host_ptr(a), 0))
@@ -417,7 +432,11 @@ class Lattice:
         return rho, u
 
     def moments_device(self, rho, ux=None, uy=None, uz=None):
-        ptr = lambda t: None if t is None else t.data_ptr()
+        """rho and u_b into CUDA float64 tensors of nx*ny*nz values (any may be
+        None)."""
+        def ptr(t):
+            return None if t is None else _device_tensor(t, self.n, "moments_device")
+
         self._check(lbm_moments(self.ctx, ptr(rho), ptr(ux), ptr(uy), ptr(uz), 1))
 
     def diag(self, rho_l, rho_v, raise_nonfinite=True):
@@ -439,27 +458,26 @@ class Lattice:
     def adjoint_forward(self, rho0, n, every):
         """Run n steps from rest with density rho0 keeping checkpoints."""
         if isinstance(rho0, np.ndarray):
-            a = np.ascontiguousarray(rho0, dtype=np.float64)
+            a = _host_array(rho0, self.n, "adjoint_forward")
             self._check(lbm_adjoint_forward(self.ctx, _host_ptr(a), 0, int(n), int(every)))
         else:
-            assert rho0.is_cuda and rho0.is_contiguous() and rho0.numel() == self.n
-            self._check(lbm_adjoint_forward(self.ctx, rho0.data_ptr(), 1, int(n), int(every)))
+            self._check(lbm_adjoint_forward(self.ctx, _device_tensor(rho0, self.n, "adjoint_forward"), 1, int(n),
+                                            int(every)))
 
     def adjoint_backward(self, dJdrho, out=None):
         """Returns (dJ/drho0, dJ/dG, dJ/dtau); dJdrho and out may be numpy
         arrays or CUDA float64 tensors."""
         dG, dT = ctypes.c_double(), ctypes.c_double()
         if isinstance(dJdrho, np.ndarray):
-            g = np.ascontiguousarray(dJdrho, dtype=np.float64)
+            g = _host_array(dJdrho, self.n, "adjoint_backward")
             gp, gdev = _host_ptr(g), 0
         else:
-            assert dJdrho.is_cuda and dJdrho.is_contiguous()
-            gp, gdev = dJdrho.data_ptr(), 1
+            gp, gdev = _device_tensor(dJdrho, self.n, "adjoint_backward"), 1
         if out is None:
             res = np.empty(self.shape)
             op, odev = _host_ptr(res), 0
         else:
-            res, op, odev = out, out.data_ptr(), 1
+            res, op, odev = out, _device_tensor(out, self.n, "adjoint_backward out"), 1
         self._check(lbm_adjoint_backward(self.ctx, gp, gdev, op, odev, ctypes.byref(dG), ctypes.byref(dT)))
         return res, dG.value, dT.value
 

@@ -167,3 +167,17 @@ int main(void) {
                     "-L", pkg, "-llbm_sc", f"-Wl,-rpath,{pkg}"], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0 and out.stdout.strip() == "ok", (out.returncode, out.stdout, out.stderr)
+
+
+def test_binding_argument_checks():
+    """Wrong host sizes and non-CUDA / wrong-dtype tensors raise before any
+    pointer reaches the library (checks that survive python -O)."""
+    import torch
+    a = lbm._host_array(np.ones((2, 3, 4), dtype=np.float32), 24, "x")
+    assert a.dtype == np.float64 and a.flags.c_contiguous and a.size == 24
+    with pytest.raises(ValueError):
+        lbm._host_array(np.ones(23), 24, "x")
+    with pytest.raises(TypeError):
+        lbm._device_tensor(torch.ones(24, dtype=torch.float64), 24, "x")  # CPU tensor
+    with pytest.raises(TypeError):
+        lbm._device_tensor([1.0] * 24, 24, "x")
