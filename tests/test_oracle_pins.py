@@ -112,6 +112,51 @@ def test_force_sums_to_zero_on_periodic_box():
     assert np.abs(Fu).max() < 1e-15
 
 
+
+def test_reported_velocity_is_half_the_force_over_rho_at_rest():
+    """Populations at rest (f = w rho, j = 0) with psi = a + b sin(k x): the
+    reported velocity of Eq. barycentric is u_b = F / (2 rho) with F the
+    closed form above; a moving uniform state reports its own velocity.
+    Catches a missing or doubled half-force term or a dropped 1/rho."""
+    L = 8
+    k = 2 * math.pi / L
+    a, b, G = 0.5, 0.2, -5.5
+    x = np.indices((3, 4, L))[2].astype(float)
+    psi = a + b * np.sin(k * x)
+    rho = _rho_for_psi(psi)
+    _, ub = o.macroscopic(o.init_populations(rho), o.Params(G=G))
+    Fx = -G * psi * b * np.cos(k * x) * math.sin(k) / 3.0
+    assert np.abs(ub[0] - Fx / (2.0 * rho)).max() < 1e-14
+    assert np.abs(ub[1]).max() < 1e-15 and np.abs(ub[2]).max() < 1e-15
+    u = np.array([0.03, -0.02, 0.05])
+    f = o.equilibrium(np.full((3, 4, 5), 1.7), np.broadcast_to(u[:, None, None, None], (3, 3, 4, 5)))
+    _, ub = o.macroscopic(f, o.Params(G=G))
+    assert np.abs(ub - u[:, None, None, None]).max() < 1e-15
+
+
+def test_slice_diagnostics_by_brute_force():
+    """Per-slice liquid area and maximum density against explicit loops over
+    a non-cubic box with values below rho_v, between and above rho_l (the
+    clamp), plus the exact special cases all-liquid / all-vapour.  Catches a
+    reduction over the wrong axes, an unclamped or inverted phase fraction."""
+    rl, rv = 2.0, 0.2
+    rng = np.random.default_rng(7)
+    nz, ny, nx = 5, 3, 4
+    rho = rng.uniform(0.0, 2.5, size=(nz, ny, nx))
+    area, mx = o.slice_diagnostics(rho, rl, rv)
+    for z in range(nz):
+        tot, m = 0.0, -1.0
+        for y in range(ny):
+            for xx in range(nx):
+                r = rho[z, y, xx]
+                frac = (r - rv) / (rl - rv)
+                tot += 0.0 if frac < 0.0 else (1.0 if frac > 1.0 else frac)
+                m = r if r > m else m
+        assert abs(area[z] - tot) < 1e-13 and mx[z] == m
+    a1, _ = o.slice_diagnostics(np.full((2, 3, 4), rl), rl, rv)
+    a0, _ = o.slice_diagnostics(np.full((2, 3, 4), rv), rl, rv)
+    assert np.all(a1 == 12.0) and np.all(a0 == 0.0)
+
 # -------------------------------------------------------------- streaming
 def test_streaming_moves_each_population_by_its_velocity():
     """Eq. LBE: f_a(x + c_a, t + 1) = f*_a(x, t), with periodic wrap."""
