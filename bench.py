@@ -80,6 +80,9 @@ def parse_args():
     ap.add_argument("--series", action="store_true",
                     help="paper form: also report the neck-radius and perturbation time series, the interface "
                          "silhouettes at t* = 7, 8, 9 and the linearity of the final pinch")
+    ap.add_argument("--components", action="store_true",
+                    help="paper form: also count the drops of the final state in 3D (connected components of "
+                         "the liquid; reads the full density and velocity fields back to the host)")
     ap.add_argument("--tau0", type=float, default=0.75, help="calibrate form: starting SRT relaxation time")
     ap.add_argument("--cal-tol", type=float, default=0.01,
                     help="calibrate form: stop when two consecutive sigma agree to this fraction")
@@ -697,7 +700,7 @@ def run_paper(args):
             L.init_ligament(float(R0), eps, rl, rv, n_waves=2)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            res = ex.breakup_run(L, R0, tcap, rl, rv, every, series=args.series)
+            res = ex.breakup_run(L, R0, tcap, rl, rv, every, series=args.series, components=args.components)
             torch.cuda.synchronize()
             wall = time.perf_counter() - t0
             cfg = L.kernel_config()
@@ -706,6 +709,7 @@ def run_paper(args):
                       "rho_l": rl, "rho_v": rv, "steps": res["steps"], "diag_every": every,
                       "drops_max": res["drops_max"], "drops_final": res["drops_final"],
                       "satellites": res["satellites"], "satellites_transient": res["satellites_transient"],
+                      "drops_3d": res.get("drops_3d"), "satellites_3d": res.get("satellites_3d"),
                       "paper_satellites": fig_sat, "T_break_over_tcap": tb,
                       "paper_T_break": fig_t, "lsa_T_break": lsa_t,
                       "rel_diff": (tb - fig_t) / fig_t if tb is not None and fig_t else None,

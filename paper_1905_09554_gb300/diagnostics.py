@@ -13,7 +13,11 @@ growth).  Pure numpy; no lattice arithmetic.
 * drops after break-up: the maximal runs (periodic in z) of slices that hold
   liquid (max rho above the mid density); with the drops on the ligament's
   axis each run is one drop, and drops beyond the number of perturbation
-  wavelengths are satellites (Fig. 2b's filled symbols).
+  wavelengths are satellites (Fig. 2b's filled symbols);
+* drops in 3D: the connected components (face neighbours, periodic in all
+  three directions) of the cells with rho above the mid density, for a
+  density field read back with lbm_moments; this also separates drops that
+  sit side by side in a slice, which the per-slice count cannot.
 """
 
 from __future__ import annotations
@@ -78,3 +82,35 @@ def count_drops(maxrho_z, rho_l, rho_v):
         return 1
     # a run starts where a liquid slice follows a dry one (wrapping around z)
     return int(np.count_nonzero(liquid & ~np.roll(liquid, 1)))
+
+
+def drop_components(rho, rho_l, rho_v):
+    """Connected components of the liquid (rho > (rho_l + rho_v)/2) of a
+    periodic (nz, ny, nx) density field, cells joined across faces and across
+    the periodic boundaries.  Returns the cell counts of the drops, largest
+    first (an empty list if there is no liquid)."""
+    from scipy import ndimage
+
+    liquid = np.asarray(rho, dtype=float) > 0.5 * (rho_l + rho_v)
+    lab, n = ndimage.label(liquid)  # face connectivity, not periodic
+    if n == 0:
+        return []
+    parent = np.arange(n + 1)
+
+    def find(i):
+        while parent[i] != i:
+            parent[i] = parent[parent[i]]
+            i = parent[i]
+        return i
+
+    for ax in range(3):
+        lo = np.take(lab, 0, axis=ax).ravel()
+        hi = np.take(lab, lab.shape[ax] - 1, axis=ax).ravel()
+        both = (lo > 0) & (hi > 0)
+        for i, j in set(zip(lo[both].tolist(), hi[both].tolist())):
+            ri, rj = find(i), find(j)
+            if ri != rj:
+                parent[max(ri, rj)] = min(ri, rj)
+    roots = np.array([find(i) for i in range(n + 1)])
+    sizes = np.bincount(roots[lab[lab > 0]], minlength=n + 1)
+    return sorted((int(v) for v in sizes if v > 0), reverse=True)

@@ -47,7 +47,8 @@ def velocity_snapshot(rho, u, rho_l, rho_v, R0, tcap, Rz):
             "z_of_max_from_neck_over_R0": dz / R0}
 
 
-def breakup_run(L, R0, tcap, rho_l, rho_v, every, series=False, max_tcap=30.0, after_tcap=1.0, n_waves=2):
+def breakup_run(L, R0, tcap, rho_l, rho_v, every, series=False, max_tcap=30.0, after_tcap=1.0, n_waves=2,
+                components=False):
     """Step `L` (already initialised) in strides of `every` steps, sampling
     `L.diag` before each stride, until some z slice holds no liquid (the
     break-up), then for `after_tcap` capillary times more while counting the
@@ -59,7 +60,10 @@ def breakup_run(L, R0, tcap, rho_l, rho_v, every, series=False, max_tcap=30.0, a
     satellites (drops beyond the n_waves main ones at the end / at most), and
     with `series` the neck-radius and mode-amplitude series, the silhouettes
     and velocity snapshots at t* = 7, 8, 9 (first sample past each) and the
-    linear fit of the final pinch."""
+    linear fit of the final pinch.  With `components` (and a break-up) the
+    final density field is read back and its drops counted in 3D
+    (`diagnostics.drop_components`): drops_3d, their cell counts, and the
+    satellites_3d beyond the n_waves main drops."""
     ts, mins, drops = [], [], []
     necks, amps, sil, vel = [], [], {}, {}
     t, broke_at, status = 0, None, 0
@@ -95,6 +99,11 @@ def breakup_run(L, R0, tcap, rho_l, rho_v, every, series=False, max_tcap=30.0, a
            "drops_max": max(drops) if drops else None, "drops_final": drops[-1] if drops else None,
            "satellites": max(0, drops[-1] - n_waves) if drops else None,
            "satellites_transient": max(0, max(drops) - n_waves) if drops else None}
+    if components and broke_at is not None and status == 0:
+        rho, _ = L.moments()
+        vols = dg.drop_components(rho, rho_l, rho_v)
+        del rho
+        out.update({"drops_3d": len(vols), "drop_volumes": vols, "satellites_3d": max(0, len(vols) - n_waves)})
     if series and ts:
         tt = np.asarray(ts[:len(necks)], dtype=float) / tcap
         a0 = amps[0] if amps and amps[0] != 0 else 1.0

@@ -51,3 +51,54 @@ def test_count_drops_counts_periodic_liquid_runs():
     assert dg.count_drops([L, V, V, L, L, V, L, L], rl, rv) == 2
     # the mid density itself is not liquid
     assert dg.count_drops([1.15, V, L, V], rl, rv) == 1
+
+
+def _flood_fill_sizes(liquid):
+    """Component sizes by breadth-first search with periodic face neighbours."""
+    nz, ny, nx = liquid.shape
+    seen = np.zeros_like(liquid, dtype=bool)
+    sizes = []
+    for start in zip(*np.nonzero(liquid)):
+        if seen[start]:
+            continue
+        seen[start] = True
+        todo, n = [start], 0
+        while todo:
+            z, y, x = todo.pop()
+            n += 1
+            for dz, dy, dx in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+                c = ((z + dz) % nz, (y + dy) % ny, (x + dx) % nx)
+                if liquid[c] and not seen[c]:
+                    seen[c] = True
+                    todo.append(c)
+        sizes.append(n)
+    return sorted(sizes, reverse=True)
+
+
+def test_drop_components_in_3d():
+    rl, rv = 2.0, 0.1
+    z, y, x = np.indices((24, 16, 20))
+
+    def ball(cz, cy, cx, r):
+        return (z - cz) ** 2 + (y - cy) ** 2 + (x - cx) ** 2 <= r * r
+
+    assert dg.drop_components(np.full((4, 4, 4), rv), rl, rv) == []
+    one = np.where(ball(12, 8, 10, 4), rl, rv)
+    assert dg.drop_components(one, rl, rv) == [int(ball(12, 8, 10, 4).sum())]
+    # a drop centred on the corner wraps across all three periodic faces
+    wrap = ball(0, 0, 0, 3) | ball(24, 0, 0, 3) | ball(0, 16, 0, 3) | ball(0, 0, 20, 3) | \
+        ball(24, 16, 0, 3) | ball(24, 0, 20, 3) | ball(0, 16, 20, 3) | ball(24, 16, 20, 3)
+    assert len(dg.drop_components(np.where(wrap, rl, rv), rl, rv)) == 1
+    # two drops side by side in the same slices: the per-slice count sees one
+    pair = ball(12, 8, 4, 3) | ball(12, 8, 15, 3)
+    rho = np.where(pair, rl, rv)
+    assert len(dg.drop_components(rho, rl, rv)) == 2
+    assert dg.count_drops(rho.max(axis=(1, 2)), rl, rv) == 1
+    # an unbroken ligament along z (closed through the periodic boundary)
+    lig = (y - 8) ** 2 + (x - 10) ** 2 <= 9
+    assert dg.drop_components(np.where(lig, rl, rv), rl, rv) == [int(lig.sum())]
+    # brute force on random sparse fields
+    rng = np.random.default_rng(11)
+    for frac in (0.15, 0.3, 0.45):
+        liq = rng.random((7, 6, 5)) < frac
+        assert dg.drop_components(np.where(liq, rl, rv), rl, rv) == _flood_fill_sizes(liq)

@@ -34,7 +34,7 @@ class Scripted:
         s = min(self.t / T_PINCH, 1.0)
         return R0 * (1.0 - s * 0.5 * (1.0 + np.cos(2 * math.pi * 2 * z / NZ)))
 
-    def diag(self, rho_l, rho_v, raise_nonfinite=True):
+    def maxrho(self):
         R = self.radius()
         maxrho = np.where(R >= 0.5, RL, RV)
         if self.t >= T_PINCH:  # two drops around z = 16, 48 plus a satellite at z = 24
@@ -43,11 +43,14 @@ class Scripted:
             maxrho[40:56] = RL
             if self.t < T_PINCH + self.sat_life:
                 maxrho[23:26] = RL
-        return {"status": 0, "maxrho_z": maxrho, "area_z": math.pi * R ** 2}
+        return maxrho
+
+    def diag(self, rho_l, rho_v, raise_nonfinite=True):
+        return {"status": 0, "maxrho_z": self.maxrho(), "area_z": math.pi * self.radius() ** 2}
 
     def moments(self):
         rho = np.full((NZ, 4, 4), RV)
-        rho[:, :2, :] = RL
+        rho[self.maxrho() == RL, :2, :] = RL  # liquid in half of each slice that holds some
         u = np.zeros((3, NZ, 4, 4))
         u[2, 5, 3, 3] = 0.7  # the fastest cell, in the vapour, at z = 5
         return rho, u
@@ -56,7 +59,7 @@ class Scripted:
 @pytest.mark.parametrize("sat_life,stable", [(40.0, 0), (500.0, 1)])
 def test_breakup_run_on_a_scripted_ligament(sat_life, stable):
     L = Scripted(sat_life)
-    res = ex.breakup_run(L, R0, TCAP, RL, RV, every=10, series=True)
+    res = ex.breakup_run(L, R0, TCAP, RL, RV, every=10, series=True, components=True)
     # break-up: first sample where a slice is dry, i.e. R < 0.5 at the neck
     # slices (z = 0, 32), s > 0.95 -> t > 807.5
     assert res["t_break"] is not None and 800.0 <= res["t_break"] <= 820.0
@@ -65,6 +68,9 @@ def test_breakup_run_on_a_scripted_ligament(sat_life, stable):
     assert res["steps"] == pytest.approx(810 + 100, abs=10)
     assert res["drops_max"] == 3 and res["satellites_transient"] == 1
     assert res["satellites"] == stable
+    # the final field read back: the same drops counted in 3D
+    assert res["drops_3d"] == 2 + stable and res["satellites_3d"] == stable
+    assert res["drop_volumes"][:2] == [16 * 8, 12 * 8]
     s = res["series"]
     assert set(s["silhouettes_R_over_R0"]) == {"7", "8"}  # t* = 9 is after the break-up
     assert len(s["silhouettes_R_over_R0"]["7"]) == NZ
@@ -86,3 +92,5 @@ def test_breakup_run_without_a_breakup_stops_at_the_limit():
     assert res["t_break"] is None and res["T_break_over_tcap"] is None
     assert res["drops_max"] is None and res["satellites"] is None
     assert res["steps"] == 350  # the first sample past 3 t_cap ends the loop
+    assert "drops_3d" not in ex.breakup_run(Still(0.0), R0, TCAP, RL, RV, every=50, max_tcap=1.0,
+                                            components=True)
