@@ -32,7 +32,7 @@ class _Rollout(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g):
         L = ctx.lattice
-        d_rho0 = torch.empty_like(g)
+        d_rho0 = torch.empty(g.shape, dtype=torch.float64, device=g.device)  # dense, x fastest
         _, dG, dtau = L.adjoint_backward(g.detach().to(torch.float64).contiguous(), out=d_rho0)
         torch.cuda.current_stream().synchronize()
         L.close()
