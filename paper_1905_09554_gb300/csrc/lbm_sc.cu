@@ -78,12 +78,21 @@ struct lbm_ctx {
 
 static thread_local char g_create_err[512];
 
+// A failed runtime call is reported through the returned status; its error
+// is also taken out of the runtime's last-error slot (a non-sticky error such
+// as an out-of-memory cudaMalloc would otherwise surface at the next launch
+// check as a launch failure).
+static lbm_status runtime_status(cudaError_t e) {
+    if (e == cudaSuccess) return LBM_OK;
+    (void)cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+}
+
 #define LBM_CUDA(ctx, call)                                                                  \
     do {                                                                                     \
         cudaError_t e_ = (call);                                                             \
         if (e_ != cudaSuccess)                                                               \
-            return (ctx)->fail(e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA,     \
-                               "%s failed: %s", #call, cudaGetErrorString(e_));              \
+            return (ctx)->fail(runtime_status(e_), "%s failed: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
 #define LBM_LAUNCHED(ctx, what)                                                              \
@@ -550,7 +559,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
                      fbytes, cudaGetErrorString(e));
             cudaFree(c->f[0]);
             delete c;
-            return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+            return runtime_status(e);
         }
         c->own_bytes += 2 * (long long)fbytes;
         cudaMemsetAsync(c->f[0], 0, fbytes, c->stream);
@@ -570,7 +579,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
             cudaFree(c->ref[1]);
             if (c->own_f) { cudaFree(c->f[0]); cudaFree(c->f[1]); }
             delete c;
-            return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+            return runtime_status(e);
         }
         c->own_bytes += 2 * (long long)rbytes;
     }
@@ -581,7 +590,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
         cudaFree(c->ref[1]);
         if (c->own_f) { cudaFree(c->f[0]); cudaFree(c->f[1]); }
         delete c;
-        return LBM_ENOMEM;
+        return runtime_status(e);
     }
     c->own_bytes += (long long)(sizeof(double) * 8 * (size_t)p->nz);
     c->diag_host.resize(8 * (size_t)p->nz);
@@ -595,7 +604,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
         cudaFree(c->ref[1]);
         if (c->own_f) { cudaFree(c->f[0]); cudaFree(c->f[1]); }
         delete c;
-        return LBM_ENOMEM;
+        return runtime_status(e);
     }
     c->own_bytes += 256;
 
@@ -1190,7 +1199,7 @@ lbm_status lbm_batch_create(const lbm_params* p, int count, const int* dims, lbm
     if (e != cudaSuccess) {
         snprintf(g_create_err, sizeof(g_create_err), "lbm_batch_create: %s", cudaGetErrorString(e));
         lbm_batch_destroy(b);
-        return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+        return runtime_status(e);
     }
     b->box.assign(count, nullptr);
     for (int i = 0; i < count; ++i) {
