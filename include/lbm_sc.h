@@ -193,7 +193,10 @@ lbm_status lbm_moments(lbm_ctx *ctx, double *rho, double *ux, double *uy,
 lbm_status lbm_diag(lbm_ctx *ctx, double rho_l, double rho_v, double *mass,
                     double mom[3], double *area_z, double *maxrho_z);
 
-/* Select the CUDA stream (cudaStream_t) for later calls. */
+/* Select the CUDA stream (cudaStream_t, NULL = legacy default) for later
+ * calls.  The previous stream is synchronised first, so work enqueued on it
+ * is complete before the new stream sees the buffers.  LBM_EINVAL for a box
+ * of a batch (it runs on the batch's stream). */
 lbm_status lbm_set_stream(lbm_ctx *ctx, void *stream);
 
 /* Checkpoint / resume.  lbm_save writes the current state (the stored

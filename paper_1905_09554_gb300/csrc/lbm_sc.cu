@@ -774,6 +774,9 @@ void lbm_destroy(lbm_ctx* c) {
 
 lbm_status lbm_set_stream(lbm_ctx* c, void* stream) {
     if (!c) return LBM_EINVAL;
+    if (c->batch) return c->fail(LBM_EINVAL, "lbm_set_stream: the boxes of a batch run on the batch's stream");
+    // work already enqueued on the old stream finishes before the new one is used
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     c->stream = static_cast<cudaStream_t>(stream);
     return LBM_OK;
 }
