@@ -49,3 +49,75 @@ def test_calibration_iteration_reaches_the_fixed_point():
     assert out["iterations"] < 40
     # stopping at 5% (the paper's criterion) takes few passes
     assert cal.calibrate_tau(98.0, measure, tau0=0.8, rel_tol=0.05)["iterations"] <= 5
+
+
+class _FakeLattice:
+    """Stands in for lbm.Lattice in the host-side measurement code: the
+    state relaxes in one step to `settle(rho0)`."""
+
+    def __init__(self, settle):
+        self.settle = settle
+        self.rho = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
+    def set_density(self, rho):
+        self.rho = np.array(rho, dtype=float)
+
+    def step(self, n):
+        self.rho = self.settle(self.rho)
+
+    def moments(self):
+        return self.rho.copy(), np.zeros((3,) + self.rho.shape)
+
+
+def test_laplace_measurement_on_sharp_droplets(monkeypatch):
+    """Host side of the Laplace test with droplets that settle to a sharp
+    ball of known radius and densities chosen so that dp = 2 sigma / R
+    exactly: the equimolar radius, the pressure jump and the fit through the
+    origin recover sigma; the free fit finds zero intercept."""
+    G, sigma, rv = -5.3, 0.05, 0.08
+    p_out = cal.pressure(rv, G)
+
+    def rho_in_for(dp):  # invert P(rho) = p_out + dp on the liquid branch
+        lo, hi = 1.5, 3.0
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            lo, hi = (mid, hi) if cal.pressure(mid, G) < p_out + dp else (lo, mid)
+        return 0.5 * (lo + hi)
+
+    def settle(rho0):
+        box = rho0.shape[0]
+        g = np.arange(box) - (box - 1) / 2.0
+        r = np.sqrt(g[:, None, None] ** 2 + g[None, :, None] ** 2 + g[None, None, :] ** 2)
+        R_init = float(np.interp(0.5 * (rho0.max() + rho0.min()), rho0[box // 2, box // 2, box // 2:][::-1],
+                                 r[box // 2, box // 2, box // 2:][::-1]))
+        inside = r <= R_init
+        R_eq = (3.0 * inside.sum() / (4.0 * math.pi)) ** (1.0 / 3.0)  # equimolar radius of the voxel ball
+        return np.where(inside, rho_in_for(2.0 * sigma / R_eq), rv)
+
+    monkeypatch.setattr(cal, "_lattice", lambda *a, **k: _FakeLattice(settle))
+    out = cal.laplace_sigma(G, 1.0, radii=(10.0, 14.0, 18.0), check_every=1, max_steps=3)
+    assert out["sigma"] == pytest.approx(sigma, rel=1e-9)
+    assert out["sigma_fit"] == pytest.approx(sigma, rel=1e-6) and abs(out["intercept"]) < 1e-8
+    assert out["rho_out"] == [pytest.approx(rv)] * 3
+    for R, R_asked in zip(out["radii"], (10.0, 14.0, 18.0)):
+        assert abs(R - R_asked) < 0.5  # the voxel ball's equimolar radius
+
+
+def test_flat_coexistence_reads_the_middle_of_each_phase(monkeypatch):
+    """The slab's liquid density is read at the box centre and the vapour at
+    z = 0, after the state stops changing."""
+    def settle(rho0):
+        nz = rho0.shape[0]
+        z = np.arange(nz)
+        liquid = np.abs(z - (nz - 1) / 2.0) < nz / 4.0
+        return np.broadcast_to(np.where(liquid, 2.1, 0.078)[:, None, None], rho0.shape).copy()
+
+    monkeypatch.setattr(cal, "_lattice", lambda *a, **k: _FakeLattice(settle))
+    rl, rv, steps = cal.flat_coexistence(-5.3, 1.0, check_every=10, max_steps=100)
+    assert (rl, rv) == (2.1, 0.078) and steps == 20  # one change, then one quiet check
