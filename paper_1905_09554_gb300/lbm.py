@@ -299,13 +299,20 @@ def _device_tensor(t, numel, what):
 
 def _params(G=-5.5, tau=1.0, collision="srt", rates=None, storage="f32", rho0=1.0, rho_ref=1.0,
             dev_scale=1.0, zchunk=0, tile_y=0, kernel=0):
+    if collision not in COLLISION:
+        raise ValueError(f"collision must be one of {sorted(COLLISION)}, got {collision!r}")
+    if storage not in STORAGE:
+        raise ValueError(f"storage must be one of {sorted(STORAGE)}, got {storage!r}")
     p = lbm_params_default()
     p.G, p.tau, p.rho0 = float(G), float(tau), float(rho0)
     p.collision = COLLISION[collision]
     if rates is not None:
+        rates = [float(v) for v in rates]
+        if len(rates) != 19:
+            raise ValueError(f"rates: expected 19 MRT rates, got {len(rates)}")
         p.has_rates = 1
         for k, v in enumerate(rates):
-            p.s[k] = float(v)
+            p.s[k] = v
     p.storage = STORAGE[storage]
     p.rho_ref, p.dev_scale = float(rho_ref), float(dev_scale)
     p.zchunk, p.tile_y, p.kernel = int(zchunk), int(tile_y), int(kernel)
@@ -327,17 +334,8 @@ class Lattice:
                  storage="f32", rho0=1.0, rho_ref=1.0, dev_scale=1.0,
                  torch_buffers=True, stream=None, zchunk=0, tile_y=0, kernel=0, test_stall=0, G2=0.0):
         lib = load()
-        p = lbm_params_default()
+        p = _params(G, tau, collision, rates, storage, rho0, rho_ref, dev_scale, zchunk, tile_y, kernel)
         p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
-        p.G, p.tau, p.rho0 = float(G), float(tau), float(rho0)
-        p.collision = COLLISION[collision]
-        if rates is not None:
-            p.has_rates = 1
-            for k, v in enumerate(rates):
-                p.s[k] = float(v)
-        p.storage = STORAGE[storage]
-        p.rho_ref, p.dev_scale = float(rho_ref), float(dev_scale)
-        p.zchunk, p.tile_y, p.kernel = int(zchunk), int(tile_y), int(kernel)
         p.test_stall = int(test_stall)
         p.G2 = float(G2)
         self.shape = (int(nz), int(ny), int(nx))

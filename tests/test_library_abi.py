@@ -181,3 +181,30 @@ def test_binding_argument_checks():
         lbm._device_tensor(torch.ones(24, dtype=torch.float64), 24, "x")  # CPU tensor
     with pytest.raises(TypeError):
         lbm._device_tensor([1.0] * 24, 24, "x")
+
+
+def test_lattice_keywords_reach_the_params(monkeypatch):
+    """Every Lattice keyword lands in its lbm_params field (captured at
+    lbm_create, which is made to refuse so that no device work starts)."""
+    seen = {}
+
+    def fake_create(p):
+        seen["p"] = p
+        return lbm.LBM_EINVAL, None
+
+    monkeypatch.setattr(lbm, "lbm_create", fake_create)
+    rates = [0.5 + 0.05 * k for k in range(19)]
+    with pytest.raises(lbm.LbmError):
+        lbm.Lattice(7, 5, 3, G=-4.0, tau=0.8, collision="mrt", rates=rates, storage="bf16l", rho0=1.5,
+                    rho_ref=0.9, dev_scale=2.0, torch_buffers=False, zchunk=12, tile_y=8, kernel=3,
+                    test_stall=1, G2=0.25)
+    p = seen["p"]
+    assert (p.nx, p.ny, p.nz) == (7, 5, 3)
+    assert (p.G, p.tau, p.rho0, p.rho_ref, p.dev_scale, p.G2) == (-4.0, 0.8, 1.5, 0.9, 2.0, 0.25)
+    assert p.collision == lbm.LBM_MRT_GUO and p.storage == lbm.LBM_BF16_LOCAL
+    assert p.has_rates == 1 and list(p.s) == pytest.approx(rates)
+    assert (p.zchunk, p.tile_y, p.kernel, p.test_stall) == (12, 8, 3, 1)
+    with pytest.raises(ValueError):
+        lbm.Lattice(4, 4, 4, collision="mrt", rates=[1.0] * 18, torch_buffers=False)
+    with pytest.raises(ValueError):
+        lbm.Lattice(4, 4, 4, storage="f8", torch_buffers=False)
