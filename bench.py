@@ -204,7 +204,7 @@ def oracle_mlups(w, args, slab, min_seconds, max_steps):
     cpu = (c1.user - c0.user) + (c1.system - c0.system)
     cells = rho.size
     assert np.isfinite(f).all()
-    desc = (f"FP64 numpy reference, {steps} steps of a {w['nx']}x{w['ny']}x{slab} periodic z-slab of the "
+    desc = (f"FP64 numpy oracle, {steps} steps of a {w['nx']}x{w['ny']}x{slab} periodic z-slab of the "
             f"workload's initial ligament ({cells} cells)")
     return cells * steps / dt / 1e6, max(1, round(cpu / dt)), desc, steps
 
@@ -255,7 +255,7 @@ def run_reference(args):
     c1 = os.times()
     cores = max(1, round(((c1.user - c0.user) + (c1.system - c0.system)) / dt))
     value = rho.size * args.steps / dt / 1e6
-    sample = (f"FP64 numpy reference; each step is a {w['nx']}x{w['ny']}x{slab} periodic z-slab "
+    sample = (f"FP64 numpy oracle; each step is a {w['nx']}x{w['ny']}x{slab} periodic z-slab "
               f"({rho.size} cells) of the workload's initial ligament")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,

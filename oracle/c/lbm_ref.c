@@ -2,7 +2,7 @@
  * Plain FP64 C reference of the single-belt Shan-Chen D3Q19 step with the
  * SRT velocity-shift collision (Sec. 2 of arXiv:1905.09554), OpenMP over z
  * planes.  TEST INFRASTRUCTURE ONLY, like the rest of oracle/: it times the
- * method on the host cores beside the numpy reference (same definition, same
+ * method on the host cores beside the numpy oracle (same definition, same
  * velocity order, same layout) and is checked against it; the library never
  * uses it, and it shares nothing with the CUDA sources.
  *

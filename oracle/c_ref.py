@@ -1,10 +1,10 @@
 """Loader of the OpenMP C reference step (oracle/c/lbm_ref.c): the SRT
 velocity-shift Shan-Chen step of Sec. 2 in plain FP64 C, for timing the
-method on all host cores beside the numpy reference.
+method on all host cores beside the numpy oracle.
 
 TEST INFRASTRUCTURE ONLY, like the rest of ``oracle/``.  `build()` compiles
 ``oracle/liblbm_ref.so`` with the host C compiler (gcc -fopenmp); `run_srt`
-takes populations in the numpy reference's layout and velocity order.
+takes populations in the numpy oracle's layout and velocity order.
 """
 
 from __future__ import annotations

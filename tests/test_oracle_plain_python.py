@@ -1,7 +1,7 @@
 """A second, numpy-free restatement of the step (plain Python lists and
-loops, `math.exp`) on tiny periodic boxes, against the numpy reference.
+loops, `math.exp`) on tiny periodic boxes, against the numpy oracle.
 
-It is written from the definitions, not from the reference's code paths:
+It is written from the definitions, not from the oracle's code paths:
 neighbours by explicit modular indexing instead of array rolls, the MRT
 collision as a sum of projections on the orthogonal d'Humieres moments
 (f* = f + sum_k M_k [ -s_k (m_k - m_k^eq) + (1 - s_k / 2) (M S)_k ] / |M_k|^2)
@@ -103,7 +103,7 @@ def plain_step(f, dims, G, coll, tau, s):
 
 
 def to_numpy(f, dims):
-    """Plain layout -> the reference's (19, nz, ny, nx) in its own velocity order."""
+    """Plain layout -> the oracle's (19, nz, ny, nx) in its own velocity order."""
     nx, ny, nz = dims
     out = np.empty((19, nz, ny, nx))
     for q, c in enumerate(o.C):
@@ -116,7 +116,7 @@ def to_numpy(f, dims):
 
 
 @pytest.mark.parametrize("coll,tau", [("srt", 1.0), ("srt", 0.7), ("mrt", 0.8), ("mrt", 1.3)])
-def test_plain_python_step_matches_the_numpy_reference(coll, tau):
+def test_plain_python_step_matches_the_numpy_oracle(coll, tau):
     dims = (3, 4, 5)
     nx, ny, nz = dims
     rng = random.Random(17)
@@ -126,7 +126,7 @@ def test_plain_python_step_matches_the_numpy_reference(coll, tau):
           for _ in range(ny)] for _ in range(nz)]
     s = [rng.uniform(0.6, 1.8) for _ in range(19)] if coll == "mrt" else None
     f_np = to_numpy(f, dims)
-    # rates follow the reference's moment order, which is the one used here
+    # rates follow the oracle's moment order, which is the one used here
     p = o.Params(G=G, tau=tau, collision=coll, s=np.array(s) if s else None)
     for _ in range(2):
         f = plain_step(f, dims, G, coll, tau, s)
