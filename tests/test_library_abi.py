@@ -41,7 +41,7 @@ def test_defaults(lib):
 
 
 def test_library_lattice_is_d3q19_with_textbook_weights(lib):
-    """The library's own velocity table is the same set as the reference's,
+    """The library's own velocity table is the same set as the oracle's,
     with the same weight per velocity (order may differ)."""
     c, w = lbm.lbm_velocities()
     lib_map = {tuple(v): wi for v, wi in zip(c, w)}
