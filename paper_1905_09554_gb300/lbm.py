@@ -511,12 +511,57 @@ class _BoxView(Lattice):
         raise LbmError(LBM_EINVAL, "boxes of a batch are stepped together with Batch.step")
 
 
+def _tune_key(dims, kw):
+    """Cache key of a batch's launch-shape pick: the boxes, the physics
+    keywords and the GPU model."""
+    import hashlib
+    import json
+    try:
+        import torch
+        gpu = torch.cuda.get_device_name() if torch.cuda.is_available() else "none"
+    except Exception:
+        gpu = "none"
+    blob = json.dumps({"dims": [[int(v) for v in d] for d in dims], "gpu": gpu,
+                       "params": {k: kw[k] for k in sorted(kw) if k not in ("tile_y", "zchunk")}},
+                      sort_keys=True, default=str)
+    return hashlib.sha256(blob.encode()).hexdigest()[:20]
+
+
+def _read_tune_cache(path):
+    import json
+    try:
+        with open(path) as fh:
+            data = json.load(fh)
+        return data if isinstance(data, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def _write_tune_cache(path, data):
+    import json
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as fh:
+        json.dump(data, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
 class Batch:
     """Independent periodic boxes (dims: list of (nx, ny, nz)) advanced
-    together; the physics keywords are those of Lattice (FP32/FP64 only)."""
+    together; the physics keywords are those of Lattice (FP32/FP64 only).
 
-    def __init__(self, dims, stream=None, **kw):
+    tune_cache: path of a JSON file of launch-shape picks.  When given (and
+    neither tile_y nor zchunk is), a pick stored for the same boxes, physics
+    and GPU model is used; otherwise the batch is autotuned once at creation
+    (lbm_batch_tune, before any state is set) and its pick stored."""
+
+    def __init__(self, dims, stream=None, tune_cache=None, trial_steps=3, **kw):
         load()
+        key = cached = None
+        if tune_cache is not None and "tile_y" not in kw and "zchunk" not in kw:
+            key = _tune_key(dims, kw)
+            cached = _read_tune_cache(tune_cache).get(key)
+            if cached:
+                kw = dict(kw, tile_y=int(cached["tile_y"]), zchunk=int(cached["zchunk"]))
         p = _params(**kw)
         if stream is not None:
             p.stream = int(stream)
@@ -535,6 +580,11 @@ class Batch:
             st, v = lbm_batch_box(b, i)
             self._check(st)
             self.boxes.append(_BoxView(self, i, v, (nz, ny, nx)))
+        if key is not None and not cached:
+            best = self.tune(trial_steps)
+            data = _read_tune_cache(tune_cache)
+            data[key] = {"tile_y": best["tile_y"], "zchunk": best["zchunk"], "ms_per_step": best["ms_per_step"]}
+            _write_tune_cache(tune_cache, data)
 
     def _check(self, st):
         if st != LBM_OK:

@@ -208,3 +208,37 @@ def test_lattice_keywords_reach_the_params(monkeypatch):
         lbm.Lattice(4, 4, 4, collision="mrt", rates=[1.0] * 18, torch_buffers=False)
     with pytest.raises(ValueError):
         lbm.Lattice(4, 4, 4, storage="f8", torch_buffers=False)
+
+
+def test_batch_tune_cache(monkeypatch, tmp_path):
+    """Batch(tune_cache=...) tunes once and stores the pick; a second batch
+    with the same boxes and physics is created with the stored launch shape
+    and does not tune; other physics get their own entry.  (The library
+    calls are stand-ins: no device work.)"""
+    calls = {"create": [], "tune": 0}
+
+    def fake_create(p, dims):
+        calls["create"].append((p.tile_y, p.zchunk))
+        return lbm.LBM_OK, ctypes.c_void_p(1)
+
+    def fake_tune(b, trial_steps):
+        calls["tune"] += 1
+        return lbm.LBM_OK, {"tile_y": 16, "zchunk": 64, "ms_per_step": 0.5}
+
+    monkeypatch.setattr(lbm, "lbm_batch_create", fake_create)
+    monkeypatch.setattr(lbm, "lbm_batch_box", lambda b, i: (lbm.LBM_OK, ctypes.c_void_p(2 + i)))
+    monkeypatch.setattr(lbm, "lbm_batch_tune", fake_tune)
+    monkeypatch.setattr(lbm, "lbm_batch_destroy", lambda b: None)
+    cache = str(tmp_path / "tune.json")
+    dims = [(16, 16, 40), (24, 24, 60)]
+    lbm.Batch(dims, tune_cache=cache, G=-5.5, tau=1.0).close()
+    assert calls["tune"] == 1 and calls["create"][-1] == (0, 0)
+    lbm.Batch(dims, tune_cache=cache, G=-5.5, tau=1.0).close()
+    assert calls["tune"] == 1 and calls["create"][-1] == (16, 64)
+    lbm.Batch(dims, tune_cache=cache, G=-5.5, tau=0.8).close()
+    assert calls["tune"] == 2 and calls["create"][-1] == (0, 0)
+    import json
+    assert len(json.load(open(cache))) == 2
+    # explicit launch shapes bypass the cache
+    lbm.Batch(dims, tune_cache=cache, tile_y=8, zchunk=32).close()
+    assert calls["tune"] == 2 and calls["create"][-1] == (8, 32)
