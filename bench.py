@@ -126,6 +126,23 @@ def mrt_rates(args):
     return s
 
 
+def host_info():
+    """Host CPU of the run (model, architecture, logical CPUs)."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                key = ln.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu": model or platform.processor() or None, "arch": platform.machine(),
+            "logical_cpus": os.cpu_count()}
+
+
 def measured_hbm():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -264,6 +281,7 @@ def run_reference(args):
         "data": "synthetic", "config": {"workload": w["name"], "sample_cells": rho.size},
         "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "host": host_info(),
     }), flush=True)
 
 
@@ -426,7 +444,7 @@ def run_ours(args):
                          f"{19 * BYTES_PER_POP[args.storage] * ncell / 1e9:.2f} GB each)",
                    "mass_rel_drift": mass_drift},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps, "host": host_info(),
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
