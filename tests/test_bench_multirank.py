@@ -94,6 +94,7 @@ def test_reference_arm_prints_the_contract_line_and_other_ranks_stay_silent():
     assert "workload" in d["config"]
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert set(d["e2e"]) == {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
+    assert d["host"]["logical_cpus"] >= 1 and d["host"]["arch"]
     out1 = subprocess.run(cmd, capture_output=True, text=True, env=dict(os.environ, RANK="1"), timeout=600,
                           cwd=ROOT)
     assert out1.returncode == 0 and out1.stdout.strip() == ""
