@@ -220,6 +220,18 @@ lbm_status lbm_set_stream(lbm_ctx *ctx, void *stream);
 lbm_status lbm_save(lbm_ctx *ctx, const char *path);
 lbm_status lbm_load(lbm_ctx *ctx, const char *path);
 
+/* Header of a checkpoint written by lbm_save, read on the host alone (no
+ * context, no CUDA call): dims = (nx, ny, nz), storage (lbm_storage),
+ * collision (lbm_collision), the step count t, G and tau.  With verify != 0
+ * the whole file is read and its checksum checked as lbm_load does.  Any
+ * output pointer may be NULL.  Returns LBM_EINVAL for a NULL or empty path,
+ * LBM_EIO if the file cannot be read, is not a version-1 checkpoint, has an
+ * inconsistent header, or (verify) is truncated, has trailing bytes or fails
+ * the checksum; the message is then in lbm_last_error(NULL). */
+lbm_status lbm_checkpoint_info(const char *path, int verify, int dims[3],
+                               int *storage, int *collision, long *t,
+                               double *G, double *tau);
+
 /* Bytes of device memory the context allocated itself. */
 long long lbm_device_bytes(const lbm_ctx *ctx);
 

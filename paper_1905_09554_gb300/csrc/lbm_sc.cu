@@ -1717,4 +1717,56 @@ lbm_status lbm_load(lbm_ctx* c, const char* path) {
     return LBM_OK;
 }
 
+lbm_status lbm_checkpoint_info(const char* path, int verify, int dims[3], int* storage, int* collision, long* t,
+                               double* G, double* tau) {
+    g_create_err[0] = 0;
+    if (!path || !path[0]) return create_fail(LBM_EINVAL, "lbm_checkpoint_info: empty path");
+    FILE* fp = fopen(path, "rb");
+    if (!fp) return create_fail(LBM_EIO, "lbm_checkpoint_info: cannot open the file");
+    struct Closer {
+        FILE* f;
+        ~Closer() { fclose(f); }
+    } closer{fp};
+    unsigned char head[256];
+    if (fread(head, 1, sizeof(head), fp) != sizeof(head))
+        return create_fail(LBM_EIO, "lbm_checkpoint_info: truncated header");
+    CkptHeader h;
+    memcpy(&h, head, sizeof(h));
+    if (memcmp(h.magic, "LBMSCKP", 8) != 0 || h.version != 1 || h.header_bytes != 256)
+        return create_fail(LBM_EIO, "lbm_checkpoint_info: not a version-1 checkpoint");
+    const uint64_t n = (uint64_t)(h.nx > 0 ? h.nx : 0) * (uint64_t)(h.ny > 0 ? h.ny : 0) * (uint64_t)(h.nz > 0 ? h.nz : 0);
+    const uint64_t elem = h.storage == LBM_F64 ? 8 : (h.storage == LBM_F32 ? 4 : 2);
+    const bool local = h.storage >= LBM_F16_LOCAL;
+    if (n == 0 || h.storage < LBM_F64 || h.storage > LBM_BF16_LOCAL || h.t < 0 ||
+        h.pop_bytes != (uint64_t)Q * n * elem || h.ref_bytes != (local ? sizeof(float) * n : 0))
+        return create_fail(LBM_EIO, "lbm_checkpoint_info: inconsistent header");
+    if (verify) {
+        Fnv64 fnv;
+        fnv.add(head, sizeof(head));
+        std::vector<unsigned char> buf(size_t(1) << 20);
+        uint64_t left = h.pop_bytes + h.ref_bytes;
+        while (left) {
+            const size_t len = left < buf.size() ? (size_t)left : buf.size();
+            if (fread(buf.data(), 1, len, fp) != len) return create_fail(LBM_EIO, "lbm_checkpoint_info: truncated file");
+            fnv.add(buf.data(), len);
+            left -= len;
+        }
+        uint64_t sum = 0;
+        if (fread(&sum, 1, 8, fp) != 8) return create_fail(LBM_EIO, "lbm_checkpoint_info: truncated file");
+        if (sum != fnv.finish()) return create_fail(LBM_EIO, "lbm_checkpoint_info: checksum mismatch");
+        if (fgetc(fp) != EOF) return create_fail(LBM_EIO, "lbm_checkpoint_info: trailing bytes");
+    }
+    if (dims) {
+        dims[0] = h.nx;
+        dims[1] = h.ny;
+        dims[2] = h.nz;
+    }
+    if (storage) *storage = h.storage;
+    if (collision) *collision = h.collision;
+    if (t) *t = (long)h.t;
+    if (G) *G = h.G;
+    if (tau) *tau = h.tau;
+    return LBM_OK;
+}
+
 }  // extern "C"

@@ -79,6 +79,10 @@ _SIGNATURES = {
     "lbm_set_stream": (ctypes.c_int, [_P, _P]),
     "lbm_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "lbm_load": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "lbm_checkpoint_info": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double)]),
     "lbm_device_bytes": (ctypes.c_longlong, [_P]),
     "lbm_params_sizeof": (ctypes.c_longlong, []),
     "lbm_kernel_config": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -206,6 +210,25 @@ def lbm_save(ctx, path):
 
 def lbm_load(ctx, path):
     return load().lbm_load(ctx, os.fsencode(path))
+
+
+def lbm_checkpoint_info(path, verify=True):
+    """(status, dict(dims=(nx, ny, nz), storage, collision, t, G, tau)) of a
+    checkpoint file, read on the host alone."""
+    dims = (ctypes.c_int * 3)()
+    st_, co, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_long()
+    G, tau = ctypes.c_double(), ctypes.c_double()
+    st = load().lbm_checkpoint_info(os.fsencode(path), 1 if verify else 0, dims, ctypes.byref(st_),
+                                    ctypes.byref(co), ctypes.byref(t), ctypes.byref(G), ctypes.byref(tau))
+    return st, dict(dims=tuple(dims), storage=st_.value, collision=co.value, t=t.value, G=G.value, tau=tau.value)
+
+
+def checkpoint_info(path, verify=True):
+    """Header of a checkpoint (lbm_checkpoint_info); raises LbmError on a bad file."""
+    st, info = lbm_checkpoint_info(path, verify)
+    if st != LBM_OK:
+        raise LbmError(st, lbm_last_error(None))
+    return info
 
 
 def lbm_device_bytes(ctx):

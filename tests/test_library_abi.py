@@ -242,3 +242,57 @@ def test_batch_tune_cache(monkeypatch, tmp_path):
     # explicit launch shapes bypass the cache
     lbm.Batch(dims, tune_cache=cache, tile_y=8, zchunk=32).close()
     assert calls["tune"] == 2 and calls["create"][-1] == (8, 32)
+
+
+def _fnv1a64_words(data: bytes) -> int:
+    """64-bit FNV-1a over little-endian 64-bit words, the byte tail one byte
+    at a time (the checkpoint checksum's stated definition)."""
+    h, prime, mask = 0xCBF29CE484222325, 0x100000001B3, (1 << 64) - 1
+    full = len(data) // 8 * 8
+    for k in range(0, full, 8):
+        h = ((h ^ int.from_bytes(data[k:k + 8], "little")) * prime) & mask
+    for b in data[full:]:
+        h = ((h ^ b) * prime) & mask
+    return h
+
+
+def _checkpoint_bytes(nx, ny, nz, storage, t, G=-5.5, tau=0.9, payload_seed=0):
+    import struct
+    elem = {lbm.LBM_F64: 8, lbm.LBM_F32: 4}.get(storage, 2)
+    n = nx * ny * nz
+    pop = 19 * n * elem
+    ref = 4 * n if storage >= lbm.LBM_F16_LOCAL else 0
+    head = b"LBMSCKP\0" + struct.pack("<II6iq5d19dQQ", 1, 256, nx, ny, nz, storage, 0, 0, t, G, tau, 1.0, 1.0,
+                                      1.0, *([1.0] * 19), pop, ref)
+    assert len(head) == 256
+    body = np.random.default_rng(payload_seed).integers(0, 256, pop + ref, dtype=np.uint8).tobytes()
+    return head + body + _fnv1a64_words(head + body).to_bytes(8, "little")
+
+
+def test_checkpoint_info_reads_and_verifies_files_without_a_gpu(lib, tmp_path):
+    """A checkpoint written here from the documented layout (256-byte header,
+    payload, FNV-1a checksum) is read back by the library on the host; a
+    flipped byte, a truncated file, trailing bytes and a foreign file are
+    refused with LBM_EIO when verifying."""
+    good = _checkpoint_bytes(5, 3, 7, lbm.LBM_F32, t=1234)
+    path = tmp_path / "state.ckpt"
+    path.write_bytes(good)
+    info = lbm.checkpoint_info(str(path))
+    assert info["dims"] == (5, 3, 7) and info["storage"] == lbm.LBM_F32 and info["t"] == 1234
+    assert info["G"] == -5.5 and info["tau"] == 0.9
+    local = tmp_path / "local.ckpt"  # odd payload length: the checksum's byte tail
+    local.write_bytes(_checkpoint_bytes(3, 3, 3, lbm.LBM_F16_LOCAL, t=7))
+    assert lbm.checkpoint_info(str(local))["storage"] == lbm.LBM_F16_LOCAL
+    flipped = bytearray(good)
+    flipped[300] ^= 0x10
+    for name, data in {"flipped": bytes(flipped), "truncated": good[:-9], "trailing": good + b"\0",
+                       "foreign": b"not a checkpoint" * 20}.items():
+        bad = tmp_path / name
+        bad.write_bytes(data)
+        st, _ = lbm.lbm_checkpoint_info(str(bad))
+        assert st == lbm.LBM_EIO, name
+    # the header alone is still readable without verification
+    bad = tmp_path / "flipped"
+    assert lbm.lbm_checkpoint_info(str(bad), verify=False)[0] == lbm.LBM_OK
+    assert lbm.lbm_checkpoint_info(str(tmp_path / "missing.ckpt"))[0] == lbm.LBM_EIO
+    assert lbm.lbm_checkpoint_info("")[0] == lbm.LBM_EINVAL
