@@ -72,18 +72,31 @@ def neck_energy(rho, rho_l, rho_v):
     return ((R - R.mean()) ** 2).mean()
 
 
-def total_mass(rho, rho_l=None, rho_v=None):
+def total_mass(rho):
     return rho.sum()
 
 
-def gradient(rho0, G, tau, steps, objective="neck", rho_l=None, rho_v=None):
+def misfit(rho, target):
+    """Density L2 misfit J = sum (rho - target)^2 / 2."""
+    return 0.5 * ((rho - target) ** 2).sum()
+
+
+def gradient(rho0, G, tau, steps, objective="neck", rho_l=None, rho_v=None, target=None):
     """(J, dJ/drho0 as a numpy (nz, ny, nx) array, dJ/dG, dJ/dtau) of the
-    objective ("neck": neck_energy with rho_l, rho_v; "mass": total mass) of
-    the density after `steps` SRT steps from rest at rho0 (numpy)."""
+    objective ("neck": neck_energy with rho_l, rho_v; "mass": total mass;
+    "misfit": L2 misfit against `target`) of the density after `steps` SRT
+    steps from rest at rho0 (numpy)."""
     r0 = torch.tensor(rho0, dtype=torch.float64, requires_grad=True)
     g = torch.tensor(float(G), dtype=torch.float64, requires_grad=True)
     t = torch.tensor(float(tau), dtype=torch.float64, requires_grad=True)
     rho = rollout(r0, g, t, steps)
-    J = neck_energy(rho, rho_l, rho_v) if objective == "neck" else total_mass(rho)
+    if objective == "neck":
+        J = neck_energy(rho, rho_l, rho_v)
+    elif objective == "mass":
+        J = total_mass(rho)
+    elif objective == "misfit":
+        J = misfit(rho, torch.tensor(target, dtype=torch.float64))
+    else:
+        raise ValueError(objective)
     J.backward()
     return float(J.detach()), r0.grad.numpy().copy(), float(g.grad), float(t.grad)

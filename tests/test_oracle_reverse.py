@@ -63,3 +63,24 @@ def test_total_mass_has_the_exact_gradient():
     rho0 = small_case()
     _, g, gG, gT = rv.gradient(rho0, G0, TAU0, 10, "mass")
     assert np.abs(g - 1.0).max() < 1e-12 and abs(gG) < 1e-10 and abs(gT) < 1e-10
+
+
+def test_density_misfit_gradient_equals_complex_step():
+    """J = sum (rho(T) - target)^2 / 2 (the density L2 misfit)."""
+    rho0 = small_case()
+    target = inputs.noisy_ligament_density(8, 8, 12, 2.2, 0.05, RL, RV, 1e-3, seed=4)
+    steps = 10
+
+    def J_np(r0, G, tau):
+        p = o.Params(G=G, tau=tau, collision="srt")
+        rho = o.run(o.init_populations(r0.astype(np.result_type(r0, G, tau))), steps, p).sum(0)
+        return 0.5 * ((rho - target) ** 2).sum()
+
+    J, g, gG, gT = rv.gradient(rho0, G0, TAU0, steps, "misfit", target=target)
+    assert abs(J - J_np(rho0, G0, TAU0)) <= 1e-12 * J
+    h = 1e-20
+    v = np.random.default_rng(8).standard_normal(rho0.shape)
+    cs = J_np(rho0 + 1j * h * v, G0, TAU0).imag / h
+    assert abs((g * v).sum() - cs) <= 1e-10 * max(1.0, abs(cs))
+    assert abs(gG - J_np(rho0, G0 + 1j * h, TAU0).imag / h) <= 1e-10 * max(1e-6, abs(gG))
+    assert abs(gT - J_np(rho0, G0, TAU0 + 1j * h).imag / h) <= 1e-10 * max(1e-6, abs(gT))

@@ -43,3 +43,25 @@ def test_adjoint_field_matches_the_reverse_mode_oracle():
     assert np.abs(g - g_ref).max() <= 1e-9 * scale, np.abs(g - g_ref).max() / scale
     assert abs(gG - gG_ref) <= 1e-9 * max(1e-6, abs(gG_ref)), (gG, gG_ref)
     assert abs(gT - gT_ref) <= 1e-9 * max(1e-6, abs(gT_ref)), (gT, gT_ref)
+
+
+def test_torch_rollout_misfit_gradient_matches_the_reverse_mode_oracle():
+    """The density L2 misfit through paper_1905_09554_gb300.autograd.rollout
+    (FP64 storage) against the reverse-mode oracle, whole field."""
+    from paper_1905_09554_gb300 import autograd as lag
+
+    rho0_np = inputs.noisy_ligament_density(12, 12, 20, 3.0, 0.1, RL, RV, 1e-3, seed=31)
+    target = inputs.noisy_ligament_density(12, 12, 20, 3.3, 0.05, RL, RV, 1e-3, seed=4)
+    steps = 20
+    rho0 = torch.tensor(rho0_np, device="cuda", requires_grad=True)
+    G = torch.tensor(G0, dtype=torch.float64, requires_grad=True)
+    tau = torch.tensor(TAU0, dtype=torch.float64, requires_grad=True)
+    rho_T = lag.rollout(rho0, G, tau, steps, every=5, storage="f64")
+    J = 0.5 * ((rho_T - torch.tensor(target, device="cuda")) ** 2).sum()
+    J.backward()
+    J_ref, g_ref, gG_ref, gT_ref = rv.gradient(rho0_np, G0, TAU0, steps, "misfit", target=target)
+    assert abs(J.item() - J_ref) <= 1e-12 * J_ref
+    g = rho0.grad.cpu().numpy()
+    assert np.abs(g - g_ref).max() <= 1e-9 * np.abs(g_ref).max()
+    assert abs(G.grad.item() - gG_ref) <= 1e-9 * max(1e-6, abs(gG_ref))
+    assert abs(tau.grad.item() - gT_ref) <= 1e-9 * max(1e-6, abs(gT_ref))
