@@ -82,7 +82,7 @@ def parse_args():
                          "silhouettes at t* = 7, 8, 9 and the linearity of the final pinch")
     ap.add_argument("--components", action="store_true",
                     help="paper form: also count the drops of the final state in 3D (connected components of "
-                         "the liquid; reads the full density and velocity fields back to the host)")
+                         "the liquid; reads the density field back to the host)")
     ap.add_argument("--tau0", type=float, default=0.75, help="calibrate form: starting SRT relaxation time")
     ap.add_argument("--cal-tol", type=float, default=0.01,
                     help="calibrate form: stop when two consecutive sigma agree to this fraction")

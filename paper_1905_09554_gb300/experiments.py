@@ -100,7 +100,7 @@ def breakup_run(L, R0, tcap, rho_l, rho_v, every, series=False, max_tcap=30.0, a
            "satellites": max(0, drops[-1] - n_waves) if drops else None,
            "satellites_transient": max(0, max(drops) - n_waves) if drops else None}
     if components and broke_at is not None and status == 0:
-        rho, _ = L.moments()
+        rho = L.density()
         vols = dg.drop_components(rho, rho_l, rho_v)
         del rho
         out.update({"drops_3d": len(vols), "drop_volumes": vols, "satellites_3d": max(0, len(vols) - n_waves)})

@@ -452,6 +452,13 @@ class Lattice:
                                 _host_ptr(u[2]), 0))
         return rho, u
 
+    def density(self):
+        """rho alone as numpy float64 (nz, ny, nx): a quarter of moments()'s
+        host memory and transfer."""
+        rho = np.empty(self.shape)
+        self._check(lbm_moments(self.ctx, _host_ptr(rho), None, None, None, 0))
+        return rho
+
     def moments_device(self, rho, ux=None, uy=None, uz=None):
         """rho and u_b into CUDA float64 tensors of nx*ny*nz values (any may be
         None)."""

@@ -48,9 +48,13 @@ class Scripted:
     def diag(self, rho_l, rho_v, raise_nonfinite=True):
         return {"status": 0, "maxrho_z": self.maxrho(), "area_z": math.pi * self.radius() ** 2}
 
-    def moments(self):
+    def density(self):
         rho = np.full((NZ, 4, 4), RV)
         rho[self.maxrho() == RL, :2, :] = RL  # liquid in half of each slice that holds some
+        return rho
+
+    def moments(self):
+        rho = self.density()
         u = np.zeros((3, NZ, 4, 4))
         u[2, 5, 3, 3] = 0.7  # the fastest cell, in the vapour, at z = 5
         return rho, u
