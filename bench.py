@@ -80,6 +80,9 @@ def parse_args():
     ap.add_argument("--series", action="store_true",
                     help="paper form: also report the neck-radius and perturbation time series, the interface "
                          "silhouettes at t* = 7, 8, 9 and the linearity of the final pinch")
+    ap.add_argument("--checkpoint-dir", default=None,
+                    help="paper form: checkpoint each run there every capillary time and resume an interrupted "
+                         "run from its checkpoint (a file holds one population copy: 61 GB at R0 = 98)")
     ap.add_argument("--components", action="store_true",
                     help="paper form: also count the drops of the final state in 3D (connected components of "
                          "the liquid; reads the density field back to the host)")
@@ -718,7 +721,12 @@ def run_paper(args):
             L.init_ligament(float(R0), eps, rl, rv, n_waves=2)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            res = ex.breakup_run(L, R0, tcap, rl, rv, every, series=args.series, components=args.components)
+            ck = None
+            if args.checkpoint_dir:
+                os.makedirs(args.checkpoint_dir, exist_ok=True)
+                ck = os.path.join(args.checkpoint_dir, f"paper_{coll}_R{R0:g}_eps{eps:g}.ckpt")
+            res = ex.breakup_run(L, R0, tcap, rl, rv, every, series=args.series, components=args.components,
+                                 checkpoint=ck)
             torch.cuda.synchronize()
             wall = time.perf_counter() - t0
             cfg = L.kernel_config()
@@ -731,7 +739,9 @@ def run_paper(args):
                       "paper_satellites": fig_sat, "T_break_over_tcap": tb,
                       "paper_T_break": fig_t, "lsa_T_break": lsa_t,
                       "rel_diff": (tb - fig_t) / fig_t if tb is not None and fig_t else None,
-                      "wall_s": wall, "glups": nx * ny * nz * res["steps"] / wall / 1e9, "kernel": cfg})
+                      "resumed_from_step": res["resumed_from_step"], "wall_s": wall,
+                      "glups": nx * ny * nz * (res["steps"] - res["resumed_from_step"]) / wall / 1e9,
+                      "kernel": cfg})
         if "series" in res:
             cases[-1]["series"] = res["series"]
             print(json.dumps({"collision": coll, "R0": R0, "eps": eps,

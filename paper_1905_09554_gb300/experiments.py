@@ -47,8 +47,35 @@ def velocity_snapshot(rho, u, rho_l, rho_v, R0, tcap, Rz):
             "z_of_max_from_neck_over_R0": dz / R0}
 
 
+def _save_progress(L, path, state):
+    """Lattice checkpoint at `path` and the run's sampled state beside it
+    (path + ".json"), each written to a temporary name and renamed."""
+    import json
+    import os
+
+    L.save(path)
+    tmp = f"{path}.json.tmp"
+    with open(tmp, "w") as fh:
+        json.dump(state, fh)
+    os.replace(tmp, path + ".json")
+
+
+def _load_progress(L, path):
+    """The sampled state saved with the checkpoint at `path` (after
+    restoring the lattice from it), or None if there is none."""
+    import json
+    import os
+
+    if not (os.path.exists(path) and os.path.exists(path + ".json")):
+        return None
+    with open(path + ".json") as fh:
+        state = json.load(fh)
+    L.load(path)
+    return state
+
+
 def breakup_run(L, R0, tcap, rho_l, rho_v, every, series=False, max_tcap=30.0, after_tcap=1.0, n_waves=2,
-                components=False):
+                components=False, checkpoint=None, checkpoint_every=None):
     """Step `L` (already initialised) in strides of `every` steps, sampling
     `L.diag` before each stride, until some z slice holds no liquid (the
     break-up), then for `after_tcap` capillary times more while counting the
@@ -63,11 +90,33 @@ def breakup_run(L, R0, tcap, rho_l, rho_v, every, series=False, max_tcap=30.0, a
     linear fit of the final pinch.  With `components` (and a break-up) the
     final density field is read back and its drops counted in 3D
     (`diagnostics.drop_components`): drops_3d, their cell counts, and the
-    satellites_3d beyond the n_waves main drops."""
+    satellites_3d beyond the n_waves main drops.
+
+    With `checkpoint` (a file path) the run saves the lattice (`L.save`) and
+    its sampled series (path + ".json") every `checkpoint_every` steps
+    (default: one capillary time) and, if both files exist when it starts,
+    resumes from them: an interrupted run continued this way returns what
+    the uninterrupted one would (apart from resumed_from_step, the step it
+    started at: 0 for a fresh run)."""
     ts, mins, drops = [], [], []
     necks, amps, sil, vel = [], [], {}, {}
     t, broke_at, status = 0, None, 0
+    if checkpoint is not None:
+        every_ck = int(checkpoint_every or max(every, round(tcap)))
+        state = _load_progress(L, checkpoint)
+        if state is not None:
+            t, broke_at = state["t"], state["broke_at"]
+            ts, mins, drops = state["ts"], state["mins"], state["drops"]
+            necks, amps = state["necks"], state["amps"]
+            sil = {int(k): v for k, v in state["sil"].items()}
+            vel = {int(k): v for k, v in state["vel"].items()}
+        next_ck = t + every_ck
+    t_start = t
     while t <= max_tcap * tcap:
+        if checkpoint is not None and t >= next_ck:
+            _save_progress(L, checkpoint, {"t": t, "broke_at": broke_at, "ts": ts, "mins": mins, "drops": drops,
+                                           "necks": necks, "amps": amps, "sil": sil, "vel": vel})
+            next_ck = t + every_ck
         d = L.diag(rho_l, rho_v, raise_nonfinite=False)
         status = d["status"]
         if status != 0:
@@ -94,7 +143,7 @@ def breakup_run(L, R0, tcap, rho_l, rho_v, every, series=False, max_tcap=30.0, a
         L.step(every)
         t += every
     tb = dg.breakup_time(ts, mins, rho_l, rho_v)
-    out = {"steps": t, "status": status, "t_break": tb,
+    out = {"steps": t, "status": status, "t_break": tb, "resumed_from_step": t_start,
            "T_break_over_tcap": tb / tcap if tb is not None else None,
            "drops_max": max(drops) if drops else None, "drops_final": drops[-1] if drops else None,
            "satellites": max(0, drops[-1] - n_waves) if drops else None,

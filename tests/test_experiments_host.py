@@ -34,6 +34,15 @@ class Scripted:
         s = min(self.t / T_PINCH, 1.0)
         return R0 * (1.0 - s * 0.5 * (1.0 + np.cos(2 * math.pi * 2 * z / NZ)))
 
+    def save(self, path):
+        with open(path, "w") as fh:
+            fh.write(str(self.t))
+
+    def load(self, path):
+        with open(path) as fh:
+            self.t = int(fh.read())
+        self.loaded_at = self.t
+
     def maxrho(self):
         R = self.radius()
         maxrho = np.where(R >= 0.5, RL, RV)
@@ -98,3 +107,29 @@ def test_breakup_run_without_a_breakup_stops_at_the_limit():
     assert res["steps"] == 350  # the first sample past 3 t_cap ends the loop
     assert "drops_3d" not in ex.breakup_run(Still(0.0), R0, TCAP, RL, RV, every=50, max_tcap=1.0,
                                             components=True)
+
+
+def test_breakup_run_resumes_from_its_checkpoint(tmp_path):
+    """A run interrupted mid-way (here at step 530, after checkpoints every
+    t_cap = 100 steps) and started again with the same checkpoint path
+    returns exactly what the uninterrupted run returns."""
+    want = ex.breakup_run(Scripted(40.0), R0, TCAP, RL, RV, every=10, series=True)
+
+    class Crash(Exception):
+        pass
+
+    class Interrupted(Scripted):
+        def step(self, n):
+            if self.t >= 530:
+                raise Crash()
+            super().step(n)
+
+    ck = str(tmp_path / "run.ckpt")
+    with pytest.raises(Crash):
+        ex.breakup_run(Interrupted(40.0), R0, TCAP, RL, RV, every=10, series=True, checkpoint=ck)
+    resumed = Scripted(40.0)
+    got = ex.breakup_run(resumed, R0, TCAP, RL, RV, every=10, series=True, checkpoint=ck)
+    assert want["resumed_from_step"] == 0 and got["resumed_from_step"] == 500
+    got["resumed_from_step"] = 0
+    assert got == want
+    assert resumed.loaded_at == 500  # the last checkpoint before the crash, not step 0
