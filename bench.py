@@ -230,24 +230,31 @@ def oracle_mlups(w, args, slab, min_seconds, max_steps):
 
 
 def c_reference_mlups(w, args, slab, steps):
-    """The OpenMP C reference (oracle/c/lbm_ref.c, SRT only) on the same slab,
-    all host threads: (MLUPS, threads, description), or None where it is not
-    available (no C compiler, MRT, G2 != 0)."""
-    if args.collision != "srt" or getattr(args, "G2", 0.0) != 0.0:
+    """The OpenMP C reference (oracle/c/lbm_ref.c, SRT or MRT) on the same
+    slab, all host threads: (MLUPS, threads, description), or None where it
+    is not available (no C compiler, G2 != 0)."""
+    if getattr(args, "G2", 0.0) != 0.0:
         return None
     try:
         from oracle import c_ref, lbm_oracle as o
         from paper_1905_09554_gb300 import inputs
         rho = inputs.ligament_density(w["nx"], w["ny"], slab, args.R0, 0.05, w["rho_l"], w["rho_v"])
         f = o.init_populations(rho)
-        c_ref.run_srt(f, 1, -5.5, args.tau)  # build, load, warm up
+        rates = mrt_rates(args)
+        if rates is None:
+            def run(k):
+                return c_ref.run_srt(f, k, -5.5, args.tau)
+        else:
+            def run(k):
+                return c_ref.run_mrt(f, k, -5.5, rates)
+        run(1)  # build, load, warm up
         t0 = time.perf_counter()
-        c_ref.run_srt(f, steps, -5.5, args.tau)
+        run(steps)
         dt = time.perf_counter() - t0
         n = c_ref.threads()
     except Exception:  # noqa: BLE001 - optional: no compiler or OpenMP on this host
         return None
-    desc = (f"FP64 C reference with OpenMP ({n} threads), {steps} SRT steps of the same "
+    desc = (f"FP64 C reference with OpenMP ({n} threads), {steps} {args.collision.upper()} steps of the same "
             f"{w['nx']}x{w['ny']}x{slab} slab")
     return rho.size * steps / dt / 1e6, n, desc
 

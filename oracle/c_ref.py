@@ -1,6 +1,7 @@
-"""Loader of the OpenMP C reference step (oracle/c/lbm_ref.c): the SRT
-velocity-shift Shan-Chen step of Sec. 2 in plain FP64 C, for timing the
-method on all host cores beside the numpy oracle.
+"""Loader of the OpenMP C reference step (oracle/c/lbm_ref.c): the Shan-Chen
+step of Sec. 2 (SRT with the velocity shift, or MRT with Guo forcing) in
+plain FP64 C, for timing the method on all host cores beside the numpy
+oracle.
 
 TEST INFRASTRUCTURE ONLY, like the rest of ``oracle/``.  `build()` compiles
 ``oracle/liblbm_ref.so`` with the host C compiler (gcc -fopenmp); `run_srt`
@@ -42,6 +43,9 @@ def load():
         _lib.lbm_ref_run_srt.restype = ctypes.c_int
         _lib.lbm_ref_run_srt.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+        _lib.lbm_ref_run_mrt.restype = ctypes.c_int
+        _lib.lbm_ref_run_mrt.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_void_p, ctypes.c_double, ctypes.c_int]
         _lib.lbm_ref_threads.restype = ctypes.c_int
     return _lib
 
@@ -56,6 +60,22 @@ def run_srt(f, steps, G, tau, rho0=1.0):
     out = np.empty_like(f)
     _, nz, ny, nx = f.shape
     st = load().lbm_ref_run_srt(f.ctypes.data, out.ctypes.data, nx, ny, nz, float(G), float(tau), float(rho0),
+                                int(steps))
+    if st != 0:
+        raise MemoryError("C reference: allocation failed")
+    return out
+
+
+def run_mrt(f, steps, G, rates, rho0=1.0):
+    """`steps` MRT steps (Guo forcing, 19 rates in moment order) of
+    populations f (19, nz, ny, nx), float64."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    s = np.ascontiguousarray(rates, dtype=np.float64)
+    if s.shape != (19,):
+        raise ValueError("rates: 19 values")
+    out = np.empty_like(f)
+    _, nz, ny, nx = f.shape
+    st = load().lbm_ref_run_mrt(f.ctypes.data, out.ctypes.data, nx, ny, nz, float(G), s.ctypes.data, float(rho0),
                                 int(steps))
     if st != 0:
         raise MemoryError("C reference: allocation failed")
