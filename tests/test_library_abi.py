@@ -296,3 +296,38 @@ def test_checkpoint_info_reads_and_verifies_files_without_a_gpu(lib, tmp_path):
     assert lbm.lbm_checkpoint_info(str(bad), verify=False)[0] == lbm.LBM_OK
     assert lbm.lbm_checkpoint_info(str(tmp_path / "missing.ckpt"))[0] == lbm.LBM_EIO
     assert lbm.lbm_checkpoint_info("")[0] == lbm.LBM_EINVAL
+
+
+def test_two_belt_tables_of_the_kernel_match_the_oracle(tmp_path):
+    """The E8 vectors and shell weights compiled into the two-belt kernel
+    (csrc/e8.cuh, built here as host C++) are the oracle's: the same 92
+    vectors and, per shell, the weights the oracle solves for exactly."""
+    import shutil
+    import subprocess
+
+    from oracle import multirange as mr
+
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    src = tmp_path / "e8_dump.cpp"
+    src.write_text(
+        '#include <cstdio>\n#include "e8.cuh"\n'
+        "int main() {\n"
+        "  for (int k = 0; k < lbm::mr::kNE; ++k) { auto v = lbm::mr::e8(k); std::printf(\"v %d %d %d\\n\", v.x, v.y, v.z); }\n"
+        "  for (int s = 0; s <= 9; ++s) std::printf(\"p %d %.17g %.17g\\n\", s, lbm::mr::p_e8(s), lbm::mr::w_d3q19(s));\n"
+        "  return 0;\n}\n")
+    exe = tmp_path / "e8_dump"
+    csrc = os.path.join(os.path.dirname(lbm.__file__), "csrc")
+    subprocess.run([cxx, "-std=c++17", "-D__host__=", "-D__device__=", "-I", csrc, str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()
+    vecs = sorted(tuple(int(t) for t in ln.split()[1:]) for ln in out if ln.startswith("v "))
+    assert vecs == sorted(tuple(int(t) for t in v) for v in mr.E8)
+    exact = mr.e8_weights()
+    for ln in out:
+        if ln.startswith("p "):
+            _, s, p, w = ln.split()
+            s, p, w = int(s), float(p), float(w)
+            assert p == (float(exact[s]) if s in exact else 0.0), s
+            assert w == {1: 1.0 / 18.0, 2: 1.0 / 36.0}.get(s, 0.0), s
