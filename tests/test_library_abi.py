@@ -331,3 +331,39 @@ def test_two_belt_tables_of_the_kernel_match_the_oracle(tmp_path):
             s, p, w = int(s), float(p), float(w)
             assert p == (float(exact[s]) if s in exact else 0.0), s
             assert w == {1: 1.0 / 18.0, 2: 1.0 / 36.0}.get(s, 0.0), s
+
+
+def test_lattice_and_moment_tables_of_the_kernels_match_the_oracle(tmp_path):
+    """csrc/lattice.cuh built as host C++: its velocities and weights are the
+    oracle's D3Q19 set, and its moment coefficients mrt_coef(k, q) are the
+    oracle's MRT matrix M[k, a] for the same velocity (row order included)."""
+    import shutil
+    import subprocess
+
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    src = tmp_path / "lattice_dump.cpp"
+    src.write_text(
+        '#include <cstdio>\n#include "lattice.cuh"\n'
+        "int main() {\n"
+        "  for (int q = 0; q < lbm::Q; ++q) {\n"
+        "    std::printf(\"%d %d %d %.17g\", lbm::cx(q), lbm::cy(q), lbm::cz(q), lbm::wq(q));\n"
+        "    for (int k = 0; k < lbm::Q; ++k) std::printf(\" %d\", lbm::mrt_coef(k, q));\n"
+        "    std::printf(\"\\n\");\n  }\n  return 0;\n}\n")
+    exe = tmp_path / "lattice_dump"
+    csrc = os.path.join(os.path.dirname(lbm.__file__), "csrc")
+    subprocess.run([cxx, "-std=c++17", "-D__host__=", "-D__device__=", "-D__forceinline__=inline", "-I", csrc,
+                    str(src), "-o", str(exe)], check=True)
+    rows = [ln.split() for ln in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                check=True).stdout.splitlines()]
+    assert len(rows) == 19
+    oracle_index = {tuple(int(v) for v in c): a for a, c in enumerate(o.C)}
+    seen = set()
+    for r in rows:
+        c = (int(r[0]), int(r[1]), int(r[2]))
+        a = oracle_index[c]
+        seen.add(a)
+        assert float(r[3]) == o.W[a], c
+        assert [int(v) for v in r[4:]] == [int(round(v)) for v in o.M[:, a]], c
+    assert len(seen) == 19
