@@ -367,3 +367,19 @@ def test_lattice_and_moment_tables_of_the_kernels_match_the_oracle(tmp_path):
         assert float(r[3]) == o.W[a], c
         assert [int(v) for v in r[4:]] == [int(round(v)) for v in o.M[:, a]], c
     assert len(seen) == 19
+
+
+def test_binding_constants_match_the_header():
+    """Every LBM_* enumerator the header defines has the same value in the
+    binding (status codes, lattice, collision, psi law, storage)."""
+    import re
+
+    text = re.sub(r"/\*.*?\*/", "", open(lbm.HEADER).read(), flags=re.S)
+    found = dict((k, int(v)) for k, v in re.findall(r"\b(LBM_[A-Z0-9_]+)\s*=\s*(\d+)", text))
+    assert len(found) >= 16
+    for name, value in found.items():
+        if name.startswith("LBM_NOALLOC"):
+            continue
+        assert getattr(lbm, name) == value, name
+    assert lbm.STATUS_NAMES == [k for k, _ in sorted(((k, v) for k, v in found.items()
+                                                      if k in lbm.STATUS_NAMES), key=lambda kv: kv[1])]
