@@ -383,3 +383,25 @@ def test_binding_constants_match_the_header():
         assert getattr(lbm, name) == value, name
     assert lbm.STATUS_NAMES == [k for k, _ in sorted(((k, v) for k, v in found.items()
                                                       if k in lbm.STATUS_NAMES), key=lambda kv: kv[1])]
+
+
+def test_params_field_offsets_match_the_header(tmp_path):
+    """Field by field, the ctypes mirror of lbm_params has the C struct's
+    offsets (a reordered or retyped field would pass a size check alone)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = [f[0] for f in lbm.lbm_params._fields_]
+    body = "".join(f'    printf("{n} %zu\\n", offsetof(lbm_params, {n}));\n' for n in names)
+    src = tmp_path / "offsets.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "lbm_sc.h"\nint main(void) {\n' + body
+                   + "    return 0;\n}\n")
+    exe = tmp_path / "offsets"
+    subprocess.run([cc, "-std=c99", "-I", os.path.dirname(lbm.HEADER), str(src), "-o", str(exe)], check=True)
+    got = dict(ln.split() for ln in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                   check=True).stdout.splitlines())
+    for n in names:
+        assert int(got[n]) == getattr(lbm.lbm_params, n).offset, n
