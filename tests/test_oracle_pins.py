@@ -442,6 +442,21 @@ def test_flat_interface_srt_tau1_matches_the_shift_integral():
     assert abs(rl - il) < 1.5e-3 and abs(rv - iv) < 1.5e-3
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("G,guess,tol", [(-4.5, (1.47, 0.233), 1e-5), (-4.8, (1.73, 0.156), 1e-4)])
+def test_flat_interface_guo_matches_the_stability_integral_for_wide_interfaces(G, guess, tol):
+    """With Guo forcing (MRT, every rate 1) the flat-interface densities
+    follow the psi'/psi mechanical-stability integral up to the lattice's
+    discretisation of the interface, which shrinks as the interface widens
+    toward the critical point: within 1e-5 at G = -4.5 (measured 5e-7) and
+    1e-4 at G = -4.8 (2.4e-5); at G = -5.3 (interface ~4 cells) it is 5e-4.
+    Catches a wrong psi law or force prefactor, which shift the bulk
+    densities at any width."""
+    il, iv = th.coexistence_integral(G, 0.0, guess=guess)
+    rl, rv, _ = flat_interface(G, "mrt", 1.0, il, iv, n=64)
+    assert abs(rl - il) < tol and abs(rv - iv) < tol, (rl - il, rv - iv)
+
+
 # ------------------------------------------------------------------ Laplace
 @pytest.mark.slow
 def test_laplace_law_for_static_cylinders():
