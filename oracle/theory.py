@@ -47,6 +47,11 @@ def coexistence_integral(G, eps, rho0=1.0, guess=(2.2, 0.08)):
 
     sol = optimize.fsolve(eqs, guess, xtol=1e-13, full_output=True)
     rl, rv = sol[0]
+    # fsolve returns its last iterate even when it did not converge: accept
+    # only a solution with two distinct phases that satisfies both equations
+    res = eqs((rl, rv))
+    if not (rl > rv > 0) or max(abs(res[0]), abs(res[1])) > 1e-9:
+        raise RuntimeError(f"coexistence_integral: no solution near {guess} (G = {G}, eps = {eps})")
     return float(rl), float(rv)
 
 
