@@ -1,6 +1,6 @@
 """Closed-form and continuum results used to pin the FP64 reference step.
 
-TEST INFRASTRUCTURE ONLY (imported by ``tests/`` and by the checker scripts,
+TEST INFRASTRUCTURE ONLY (imported by ``tests/`` and the scripts under tests/golden/,
 never by the library).  Nothing here runs the lattice; each function is a
 textbook or continuum statement that the lattice results are compared with.
 """

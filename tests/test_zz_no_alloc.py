@@ -20,7 +20,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
-if not torch.cuda.is_available():  # pragma: no cover - GPU machine only
+if not torch.cuda.is_available():  # pragma: no cover - CUDA device only
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 from paper_1905_09554_gb300 import inputs, lbm  # noqa: E402

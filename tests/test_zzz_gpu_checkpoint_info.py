@@ -8,7 +8,7 @@ from paper_1905_09554_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
-if not torch.cuda.is_available():  # pragma: no cover - GPU machine only
+if not torch.cuda.is_available():  # pragma: no cover - CUDA device only
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 from paper_1905_09554_gb300 import lbm  # noqa: E402
