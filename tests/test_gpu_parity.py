@@ -12,6 +12,7 @@ import math
 import numpy as np
 import pytest
 
+from oracle import initial_state as ini
 from oracle import lbm_oracle as o
 from paper_1905_09554_gb300 import inputs
 
@@ -275,13 +276,18 @@ def test_zero_steps_is_identity_and_counter():
 
 
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-14), ("f32", 1e-6)])
-def test_ligament_initial_state_kernel(storage, tol):
-    """The device-side ligament set-up equals the host input generator; the
-    state is at rest (j = 0), so the reported u_b is F/(2 rho)."""
-    nx, ny, nz = 24, 20, 30
-    want = inputs.ligament_density(nx, ny, nz, 5.0, 0.05, RL, RV)
+@pytest.mark.parametrize("box,R0,eps,width,n_waves", [
+    ((24, 20, 30), 5.0, 0.05, 2.0, 1),   # even cross-section: axis between nodes
+    ((21, 23, 17), 6.0, -0.1, 1.5, 2),   # odd, ragged, two wavelengths, other width
+])
+def test_ligament_initial_state_kernel(storage, tol, box, R0, eps, width, n_waves):
+    """The device-side ligament set-up (Sec. 3) equals the oracle's pinned
+    initial state; the state is at rest (j = 0), so the reported u_b is
+    F/(2 rho)."""
+    nx, ny, nz = box
+    want = ini.ligament_density(nx, ny, nz, R0, eps, RL, RV, width=width, n_waves=n_waves)
     with lbm.Lattice(nx, ny, nz, storage=storage) as L:
-        L.init_ligament(5.0, 0.05, RL, RV)
+        L.init_ligament(R0, eps, RL, RV, width=width, n_waves=n_waves)
         r, u = L.moments()
     r_ref, u_ref = o.macroscopic(o.init_populations(want), o.Params(G=G))
     assert np.abs(r - r_ref).max() <= tol * 3
