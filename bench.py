@@ -82,7 +82,8 @@ def parse_args():
                          "silhouettes at t* = 7, 8, 9 and the linearity of the final pinch")
     ap.add_argument("--checkpoint-dir", default=None,
                     help="paper form: checkpoint each run there every capillary time and resume an interrupted "
-                         "run from its checkpoint (a file holds one population copy: 61 GB at R0 = 98)")
+                         "run from its checkpoint (a file holds one population copy: 61 GB at R0 = 98; the "
+                         "previous file is removed only after the next one is complete)")
     ap.add_argument("--components", action="store_true",
                     help="paper form: also count the drops of the final state in 3D (connected components of "
                          "the liquid; reads the density field back to the host)")

@@ -47,30 +47,49 @@ def velocity_snapshot(rho, u, rho_l, rho_v, R0, tcap, Rz):
             "z_of_max_from_neck_over_R0": dz / R0}
 
 
+def _lattice_file(path, t):
+    return f"{path}.t{int(t)}"
+
+
 def _save_progress(L, path, state):
-    """Lattice checkpoint at `path` and the run's sampled state beside it
-    (path + ".json"), each written to a temporary name and renamed."""
+    """Checkpoint of the run: the lattice at step state["t"] in its own file
+    (path + ".t<step>"), then the sampled state, naming that file, in
+    path + ".json" (written to a temporary name and renamed), then the older
+    lattice files are removed.  The json is the commit point: a crash before
+    its rename leaves the previous json and the lattice file it names intact,
+    so a resumed run never pairs a lattice with samples of another step."""
+    import glob
     import json
     import os
 
-    L.save(path)
+    lat = _lattice_file(path, state["t"])
+    L.save(lat)
     tmp = f"{path}.json.tmp"
     with open(tmp, "w") as fh:
-        json.dump(state, fh)
+        json.dump(dict(state, lattice=os.path.basename(lat)), fh)
     os.replace(tmp, path + ".json")
+    for old in glob.glob(glob.escape(path) + ".t*"):
+        if old != lat and not old.endswith(".tmp"):
+            os.remove(old)
 
 
 def _load_progress(L, path):
-    """The sampled state saved with the checkpoint at `path` (after
-    restoring the lattice from it), or None if there is none."""
+    """The sampled state saved with the last complete checkpoint at `path`
+    (after restoring the lattice from the file it names), or None if there
+    is none.  Raises if the restored lattice is not at the state's step."""
     import json
     import os
 
-    if not (os.path.exists(path) and os.path.exists(path + ".json")):
+    if not os.path.exists(path + ".json"):
         return None
     with open(path + ".json") as fh:
         state = json.load(fh)
-    L.load(path)
+    lat = os.path.join(os.path.dirname(path), state.get("lattice", ""))
+    if not state.get("lattice") or not os.path.exists(lat):
+        return None
+    L.load(lat)
+    if L.time != state["t"]:
+        raise RuntimeError(f"checkpoint {lat} holds step {L.time}, its samples end at step {state['t']}")
     return state
 
 
@@ -92,10 +111,10 @@ def breakup_run(L, R0, tcap, rho_l, rho_v, every, series=False, max_tcap=30.0, a
     (`diagnostics.drop_components`): drops_3d, their cell counts, and the
     satellites_3d beyond the n_waves main drops.
 
-    With `checkpoint` (a file path) the run saves the lattice (`L.save`) and
-    its sampled series (path + ".json") every `checkpoint_every` steps
-    (default: one capillary time) and, if both files exist when it starts,
-    resumes from them: an interrupted run continued this way returns what
+    With `checkpoint` (a file path) the run saves the lattice (`L.save`, to
+    path + ".t<step>") and its sampled series (path + ".json") every
+    `checkpoint_every` steps (default: one capillary time) and, if a complete
+    checkpoint exists when it starts, resumes from it: an interrupted run continued this way returns what
     the uninterrupted one would (apart from resumed_from_step, the step it
     started at: 0 for a fresh run)."""
     ts, mins, drops = [], [], []

@@ -29,6 +29,10 @@ class Scripted:
     def step(self, n):
         self.t += n
 
+    @property
+    def time(self):
+        return self.t
+
     def radius(self):
         z = np.arange(NZ)
         s = min(self.t / T_PINCH, 1.0)
@@ -133,3 +137,49 @@ def test_breakup_run_resumes_from_its_checkpoint(tmp_path):
     got["resumed_from_step"] = 0
     assert got == want
     assert resumed.loaded_at == 500  # the last checkpoint before the crash, not step 0
+
+
+def test_breakup_run_resumes_after_a_crash_between_lattice_and_samples(tmp_path):
+    """A crash after the lattice of a checkpoint is written but before its
+    samples are committed: the resumed run starts from the previous complete
+    checkpoint (lattice and samples of the same step) and returns what the
+    uninterrupted run returns; no stale lattice file is left behind."""
+    want = ex.breakup_run(Scripted(40.0), R0, TCAP, RL, RV, every=10, series=True)
+
+    class Crash(Exception):
+        pass
+
+    class CrashInSave(Scripted):
+        def save(self, path):
+            super().save(path)
+            if self.t >= 500:
+                raise Crash()
+
+    ck = str(tmp_path / "run.ckpt")
+    with pytest.raises(Crash):
+        ex.breakup_run(CrashInSave(40.0), R0, TCAP, RL, RV, every=10, series=True, checkpoint=ck)
+    assert (tmp_path / "run.ckpt.t500").exists()  # written, never committed
+    resumed = Scripted(40.0)
+    got = ex.breakup_run(resumed, R0, TCAP, RL, RV, every=10, series=True, checkpoint=ck)
+    assert resumed.loaded_at == 400
+    assert got["resumed_from_step"] == 400
+    got["resumed_from_step"] = 0
+    assert got == want
+    left = sorted(p.name for p in tmp_path.iterdir())
+    assert left == ["run.ckpt.json", f"run.ckpt.t{max(int(n.split('.t')[-1]) for n in left if '.t' in n)}"]
+
+
+def test_load_progress_refuses_a_lattice_of_another_step(tmp_path):
+    import json
+
+    ck = str(tmp_path / "run.ckpt")
+    L = Scripted(0.0)
+    L.t = 300
+    ex._save_progress(L, ck, {"t": 300})
+    with open(ck + ".json") as fh:
+        state = json.load(fh)
+    state["t"] = 400
+    with open(ck + ".json", "w") as fh:
+        json.dump(state, fh)
+    with pytest.raises(RuntimeError):
+        ex._load_progress(Scripted(0.0), ck)
