@@ -174,6 +174,12 @@ lbm_status lbm_step(lbm_ctx *ctx, long n);
 /* Steps taken since the last initialisation. */
 long lbm_time(const lbm_ctx *ctx);
 
+/* Which of the two population copies holds the current state: 0 for f_a,
+ * 1 for f_b of lbm_params (or the first / second copy the context allocated
+ * itself); -1 for a NULL context.  Lets a caller that owns the copies read
+ * the stored populations directly (e.g. for lbm_diag_noalloc). */
+int lbm_current_copy(const lbm_ctx *ctx);
+
 /* Macroscopic fields of the current state (Eq. momentum): rho and the
  * barycentric velocity u_b = (sum_a c_a f_a + F/2) / rho (Eq. barycentric),
  * reported for both operators (F includes the second belt when G2 != 0).
@@ -204,10 +210,11 @@ lbm_status lbm_set_stream(lbm_ctx *ctx, void *stream);
  * the local-reference formats, the step count t and the parameters) to
  * `path` (written to path.tmp, then renamed, so an interrupted save leaves
  * an existing file intact).  lbm_load restores a state saved from a context
- * with the same box and storage (and, for the deviation formats, the same
- * rho_ref / dev_scale): stepping on from the loaded state gives bit-identical
- * results to never having stopped.  G, tau and the MRT rates stored in the
- * file are informational; the context's own are used.  File layout: a
+ * with the same box, storage (and, for the deviation formats, the same
+ * rho_ref / dev_scale) and physics (collision operator, G, tau, rho0 and the
+ * MRT rates, compared bit for bit): stepping on from the loaded state gives
+ * bit-identical results to never having stopped.  The second-belt strength
+ * G2 is not recorded in the file and not checked.  File layout: a
  * 256-byte header, the populations, the reference field, a 64-bit FNV-1a
  * checksum over 64-bit words of everything before it.  Both synchronise the
  * context's stream; both stage through 2 x 32 MiB of pinned host memory
@@ -215,8 +222,8 @@ lbm_status lbm_set_stream(lbm_ctx *ctx, void *stream);
  * Returns LBM_EIO if the file cannot be opened, written or read, is
  * truncated, has trailing bytes or fails the checksum (the context's state is
  * then unchanged: the file is read into the spare copy and made current only
- * after the checksum matches), LBM_EINVAL for a box/storage mismatch, a
- * batch box, or an empty path. */
+ * after the checksum matches), LBM_EINVAL for a box, storage or physics
+ * mismatch (state unchanged), a batch box, or an empty path. */
 lbm_status lbm_save(lbm_ctx *ctx, const char *path);
 lbm_status lbm_load(lbm_ctx *ctx, const char *path);
 

@@ -629,6 +629,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
             for (int k : rel) a.s[k] = 1.0 / p->tau;
         }
     }
+    round_params(a);
     c->coll = collision_kernel(*p, a.s);
     a.err = c->dev_err;
     a.test_stall = p->test_stall ? 1 : 0;
@@ -782,6 +783,8 @@ lbm_status lbm_set_stream(lbm_ctx* c, void* stream) {
 }
 
 long lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
+
+int lbm_current_copy(const lbm_ctx* c) { return c ? c->cur : -1; }
 
 long long lbm_device_bytes(const lbm_ctx* c) { return c ? c->own_bytes : 0; }
 
@@ -1356,6 +1359,10 @@ AdjointArgs adjoint_args(const lbm_ctx* c) {
     a.tau = c->p.tau;
     a.omega = 1.0 / c->p.tau;
     a.rho0 = c->p.rho0;
+    a.Gf = float(a.G);
+    a.tauf = float(a.tau);
+    a.omegaf = float(a.omega);
+    a.rho0f = float(a.rho0);
     const long long want = (c->n + adjoint_threads() - 1) / adjoint_threads();
     const long long cap = 8LL * c->num_sms;
     a.grid = int(want < cap ? (want < 1 ? 1 : want) : cap);
@@ -1695,6 +1702,16 @@ lbm_status lbm_load(lbm_ctx* c, const char* path) {
     if (h.storage >= LBM_F16_DEV && (h.dev_scale != mine.dev_scale ||
                                      (h.storage < LBM_F16_LOCAL && h.rho_ref != mine.rho_ref)))
         return c->fail(LBM_EINVAL, "lbm_load: %s was written with another rho_ref / dev_scale", path);
+    // the physics of the run: a state evolved under other parameters is not
+    // the state of this context (a resumed run must equal an uninterrupted one)
+    bool same_rates = true;
+    for (int k = 0; k < Q; ++k) same_rates = same_rates && h.s[k] == mine.s[k];
+    if (h.collision != mine.collision || h.G != mine.G || h.tau != mine.tau || h.rho0 != mine.rho0 || !same_rates)
+        return c->fail(LBM_EINVAL,
+                       "lbm_load: %s was written with other physics (collision %d, G %.17g, tau %.17g, rho0 %.17g%s); "
+                       "the context has collision %d, G %.17g, tau %.17g, rho0 %.17g",
+                       path, h.collision, h.G, h.tau, h.rho0, same_rates ? "" : ", other MRT rates", mine.collision,
+                       mine.G, mine.tau, mine.rho0);
     if (h.pop_bytes != mine.pop_bytes || h.ref_bytes != mine.ref_bytes || h.t < 0)
         return c->fail(LBM_EIO, "lbm_load: %s has an inconsistent header", path);
     CkptStaging stg;

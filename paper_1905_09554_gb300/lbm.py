@@ -74,6 +74,7 @@ _SIGNATURES = {
     "lbm_get_populations": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "lbm_step": (ctypes.c_int, [_P, ctypes.c_long]),
     "lbm_time": (ctypes.c_long, [_P]),
+    "lbm_current_copy": (ctypes.c_int, [_P]),
     "lbm_moments": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int]),
     "lbm_diag": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _D, _D, _D, _D]),
     "lbm_set_stream": (ctypes.c_int, [_P, _P]),
@@ -190,6 +191,10 @@ def lbm_step(ctx, n):
 
 def lbm_time(ctx):
     return load().lbm_time(ctx)
+
+
+def lbm_current_copy(ctx):
+    return load().lbm_current_copy(ctx)
 
 
 def lbm_moments(ctx, rho, ux, uy, uz, on_device):
@@ -411,6 +416,14 @@ class Lattice:
     @property
     def time(self):
         return lbm_time(self.ctx)
+
+    def stored_populations(self):
+        """The torch uint8 buffer that holds the current state exactly as
+        stored (19 * nx * ny * nz elements of the storage type, library
+        velocity order); only with torch_buffers=True."""
+        if self._bufs is None:
+            raise LbmError(LBM_EINVAL, "stored_populations: the population copies are not torch buffers")
+        return self._bufs[lbm_current_copy(self.ctx)]
 
     # -- state
     def init_ligament(self, R0, eps, rho_l, rho_v, width=2.0, n_waves=1):

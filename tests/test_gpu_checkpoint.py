@@ -5,7 +5,8 @@
   run, for every storage format (the file holds the stored bits).
 * A damaged file (flipped byte, truncation, trailing bytes, foreign file) is
   refused with LBM_EIO and leaves the context's state untouched; a file of
-  another box or storage is refused with LBM_EINVAL.
+  another box, storage or physics (G, tau, collision, rho0, MRT rates) is
+  refused with LBM_EINVAL.
 """
 
 import os
@@ -93,6 +94,30 @@ def test_mismatched_box_or_storage_is_refused(tmp_path):
         assert "box" in lbm.lbm_last_error(M.ctx)
     with lbm.Lattice(*SHAPE, G=-5.5, storage="f16") as M:
         assert lbm.lbm_load(M.ctx, path) == lbm.LBM_EINVAL
+
+
+@pytest.mark.parametrize("kw", [dict(G=-5.4), dict(tau=0.9), dict(collision="mrt"), dict(rho0=1.1),
+                                dict(collision="mrt", rates=[1.0] * 19)])
+def test_other_physics_is_refused(tmp_path, kw):
+    """A checkpoint written under other parameters (G, tau, collision, rho0,
+    MRT rates) is refused with LBM_EINVAL and the state is kept."""
+    path = str(tmp_path / "state.ckpt")
+    base = dict(G=-5.5, tau=1.0, collision="srt")
+    if kw.get("rates") is not None:  # MRT at the paper's rates vs every rate 1
+        base = dict(G=-5.5, tau=0.8, collision="mrt")
+        kw = dict(kw, tau=0.8)
+    with lbm.Lattice(*SHAPE, storage="f32", **base) as L:
+        L.init_ligament(6.0, 0.1, RL, RV)
+        L.save(path)
+    args = dict(base, **kw)
+    with lbm.Lattice(*SHAPE, storage="f32", **args) as M:
+        M.init_ligament(5.0, 0.1, RL, RV)
+        M.step(3)
+        before = M.get_populations()
+        assert lbm.lbm_load(M.ctx, path) == lbm.LBM_EINVAL
+        assert "other physics" in lbm.lbm_last_error(M.ctx)
+        assert M.time == 3
+        assert np.array_equal(M.get_populations(), before)
 
 
 def test_save_replaces_atomically(tmp_path):
