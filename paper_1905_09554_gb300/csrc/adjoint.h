@@ -9,6 +9,7 @@ struct AdjointArgs {
     int nx, ny, nz;
     long long n;
     double G, tau, omega, rho0;
+    float Gf, tauf, omegaf, rho0f;  // rounded on the host for the FP32 kernels
     int grid;  // blocks of adjoint_threads() threads (grid-stride loops)
 };
 

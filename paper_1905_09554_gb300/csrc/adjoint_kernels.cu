@@ -91,7 +91,7 @@ adj_collide_kernel(const R* __restrict__ f, const R* __restrict__ psi, const R* 
                    double* __restrict__ partials, AdjointArgs a) {
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const long long n = a.n;
-    const R G = R(a.G), tau = R(a.tau), omega = R(a.omega);
+    const R G = par<R>(a.G, a.Gf), tau = par<R>(a.tau, a.tauf), omega = par<R>(a.omega, a.omegaf);
     double accG = 0.0, accT = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const Cell c = cell_of(i, nx, ny);
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kThreads)
 adj_force_kernel(const R* __restrict__ psi, const R* __restrict__ gF, R* __restrict__ gr, AdjointArgs a) {
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const long long n = a.n;
-    const R G = R(a.G), rho0 = R(a.rho0);
+    const R G = par<R>(a.G, a.Gf), rho0 = par<R>(a.rho0, a.rho0f);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const Cell c = cell_of(i, nx, ny);
         R term = R(0);
@@ -240,7 +240,7 @@ cudaError_t run_adjoint_step(const AdjointArgs& a, const void* f, void* psi, con
                              const void* gr_next, void* lam_out, void* gr_out, void* gF, double* partials,
                              double* acc, cudaStream_t st) {
     const int grid = a.grid;
-    adj_psi_kernel<R><<<grid, kThreads, 0, st>>>(static_cast<const R*>(f), static_cast<R*>(psi), a.n, R(a.rho0));
+    adj_psi_kernel<R><<<grid, kThreads, 0, st>>>(static_cast<const R*>(f), static_cast<R*>(psi), a.n, par<R>(a.rho0, a.rho0f));
     adj_collide_kernel<R><<<grid, kThreads, 0, st>>>(static_cast<const R*>(f), static_cast<const R*>(psi),
                                                      static_cast<const R*>(lam_next), static_cast<const R*>(gr_next),
                                                      static_cast<R*>(lam_out), static_cast<R*>(gF), partials, a);

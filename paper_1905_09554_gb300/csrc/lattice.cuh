@@ -32,6 +32,15 @@ __host__ __device__ constexpr double wq(int q) {
     return q == 0 ? 1.0 / 3.0 : (cx(q) * cx(q) + cy(q) * cy(q) + cz(q) * cz(q) == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
 }
 
+// A step parameter in the arithmetic type R: the double value for FP64, its
+// float copy rounded once on the host otherwise (float(x) either way, so no
+// result bit depends on where the rounding happened).
+template <class R>
+__host__ __device__ __forceinline__ R par(double d, float f) {
+    if constexpr (sizeof(R) == sizeof(double)) return d;
+    else return f;
+}
+
 // Compile-time loop: f(std::integral_constant<int, i>) for i in [B, E).
 template <int B, int E, class F>
 __host__ __device__ __forceinline__ void static_for(F&& f) {

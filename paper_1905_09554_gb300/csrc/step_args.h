@@ -25,12 +25,33 @@ struct StepArgs {
     double tau, omega;    // SRT relaxation time and 1/tau
     double rho0, inv_rho0;
     double s[Q];          // MRT rates, moment order
+    // The same parameters rounded to float once on the host, for the float
+    // arithmetic of the 32- and 16-bit formats: a double-to-float conversion
+    // inside the cell loop would occupy the FP64 pipe (2 lanes per SM clock).
+    float Gf, tauf, omegaf, rho0f, inv_rho0f;
+    float sf[Q];
     DevParams dev;
     int* err;             // device error word (bit 0: a bounded wait timed out)
     const float* ref_src; // local-reference storage: density field of the source copy
     float* ref_dst;       // ... and of the destination copy
     int test_stall;       // failure test of the bounded waits (bulk kernel)
 };
+
+// MRT rates in the arithmetic type R (see par() in lattice.cuh).
+template <class R>
+__host__ __device__ __forceinline__ const R (&rates(const StepArgs& a))[Q] {
+    if constexpr (sizeof(R) == sizeof(double)) return a.s;
+    else return a.sf;
+}
+// Fill the float copies from the double fields.
+inline void round_params(StepArgs& a) {
+    a.Gf = float(a.G);
+    a.tauf = float(a.tau);
+    a.omegaf = float(a.omega);
+    a.rho0f = float(a.rho0);
+    a.inv_rho0f = float(a.inv_rho0);
+    for (int k = 0; k < Q; ++k) a.sf[k] = float(a.s[k]);
+}
 
 // One box of a batch: geometry, work items and where its populations start
 // (element offset) in the batch's population copies.

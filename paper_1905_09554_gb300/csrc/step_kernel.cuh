@@ -93,7 +93,7 @@ __device__ __forceinline__ void collide_srt(R (&f)[Q], R Fx, R Fy, R Fz, R tau, 
 // with the closed forms of m_eq = M f_eq and of the Guo source moments M S.
 // Conserved moments: the rho row vanishes and the j rows reduce to -F.
 template <class R>
-__device__ __forceinline__ void collide_mrt(R (&f)[Q], R Fx, R Fy, R Fz, const double (&s)[Q]) {
+__device__ __forceinline__ void collide_mrt(R (&f)[Q], R Fx, R Fy, R Fz, const R (&s)[Q]) {
     // Pair sums feed the moments that are even in c, pair differences the
     // odd ones (M[k][q+1] = +/- M[k][q] for the opposite velocity q+1).
     R ps[9], pd[9];
@@ -158,7 +158,7 @@ __device__ __forceinline__ void collide_mrt(R (&f)[Q], R Fx, R Fy, R Fz, const d
     static_for<0, Q>([&](auto kc) {
         constexpr int k = decltype(kc)::value;
         if constexpr (k != 0 && k != 3 && k != 5 && k != 7) {
-            const R sk = R(s[k]);
+            const R sk = s[k];
             d[k] = (sk * (m[k] - meq[k]) - (R(1) - R(0.5) * sk) * sg[k]) * R(1.0 / mrt_norm(k));
         }
     });
@@ -207,7 +207,7 @@ __device__ __forceinline__ void collide_mrt(R (&f)[Q], R Fx, R Fy, R Fz, const d
 // Algebraically identical to collide_mrt for such rates, with far fewer
 // operations (only the even rows of K are transformed).
 template <class R, bool UNIT>
-__device__ __forceinline__ void collide_mrt_sparse(R (&f)[Q], R Fx, R Fy, R Fz, const double (&s)[Q]) {
+__device__ __forceinline__ void collide_mrt_sparse(R (&f)[Q], R Fx, R Fy, R Fz, const R (&s)[Q]) {
     R ps[9], rho = f[0], jx = R(0), jy = R(0), jz = R(0);
     static_for<0, 9>([&](auto pc) {
         constexpr int p = decltype(pc)::value, q = 2 * p + 1;
@@ -248,7 +248,7 @@ __device__ __forceinline__ void collide_mrt_sparse(R (&f)[Q], R Fx, R Fy, R Fz, 
                 else if constexpr (c == -1) m -= ps[p];
                 else if constexpr (c != 0) m += R(c) * ps[p];
             });
-            dk[i] = (R(1) - R(s[k])) * (m - meq[i] + R(0.5) * sg[i]) * R(1.0 / mrt_norm(k));
+            dk[i] = (R(1) - s[k]) * (m - meq[i] + R(0.5) * sg[i]) * R(1.0 / mrt_norm(k));
         });
     }
     auto corr = [&](auto qc) {
@@ -323,13 +323,13 @@ __device__ __forceinline__ void update_cell(typename Codec::R (&fc)[Q], const ty
         if constexpr (cy(q) != 0) sy += R(wq(q) * cy(q)) * v;
         if constexpr (cz(q) != 0) sz += R(wq(q) * cz(q)) * v;
     });
-    const R gpsi = -R(a.G) * p0[slot];
+    const R gpsi = -par<R>(a.G, a.Gf) * p0[slot];
     const R Fx = gpsi * sx, Fy = gpsi * sy, Fz = gpsi * sz;
 
-    if constexpr (COLL == COLL_SRT) collide_srt<R>(fc, Fx, Fy, Fz, R(a.tau), R(a.omega));
-    else if constexpr (COLL == COLL_MRT) collide_mrt<R>(fc, Fx, Fy, Fz, a.s);
-    else if constexpr (COLL == COLL_MRT_SPARSE) collide_mrt_sparse<R, false>(fc, Fx, Fy, Fz, a.s);
-    else collide_mrt_sparse<R, true>(fc, Fx, Fy, Fz, a.s);
+    if constexpr (COLL == COLL_SRT) collide_srt<R>(fc, Fx, Fy, Fz, par<R>(a.tau, a.tauf), par<R>(a.omega, a.omegaf));
+    else if constexpr (COLL == COLL_MRT) collide_mrt<R>(fc, Fx, Fy, Fz, rates<R>(a));
+    else if constexpr (COLL == COLL_MRT_SPARSE) collide_mrt_sparse<R, false>(fc, Fx, Fy, Fz, rates<R>(a));
+    else collide_mrt_sparse<R, true>(fc, Fx, Fy, Fz, rates<R>(a));
 
     // Eq. LBE streaming: f_a(x + c_a, t + 1) = f*_a(x, t).
     static_for<0, Q>([&](auto qc) {
@@ -392,7 +392,7 @@ sc_step_kernel(const typename Codec::S* __restrict__ src, typename Codec::S* __r
     const long long yoff[3] = {(long long)ym * nx, (long long)gy * nx, (long long)yp * nx};
     const int xidx[3] = {xm, gx, xp};
 
-    const R rho0 = R(a.rho0), inv_rho0 = R(a.inv_rho0);
+    const R rho0 = par<R>(a.rho0, a.rho0f), inv_rho0 = par<R>(a.inv_rho0, a.inv_rho0f);
     const DevParams dev = a.dev;
 
     auto slot_of = [&](int z) { return (z - zs + 1) & (NSLOT - 1); };
@@ -542,7 +542,7 @@ sc_step_async_kernel(const typename Codec::S* __restrict__ src, typename Codec::
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const long long n = a.n;
     const long long plane = (long long)nx * ny;
-    const R rho0 = R(a.rho0), inv_rho0 = R(a.inv_rho0);
+    const R rho0 = par<R>(a.rho0, a.rho0f), inv_rho0 = par<R>(a.inv_rho0, a.inv_rho0f);
     const DevParams dev = a.dev;
     const int my_slot = (ly + 1) * PX + (lx + 1);
 
@@ -719,7 +719,7 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src_all, typename Code
 
     const int tid = threadIdx.x;
     const int lx = tid % TX, ly = tid / TX;
-    const R rho0 = R(a.rho0), inv_rho0 = R(a.inv_rho0);
+    const R rho0 = par<R>(a.rho0, a.rho0f), inv_rho0 = par<R>(a.inv_rho0, a.inv_rho0f);
     const DevParams dev = a.dev;
     const int my_slot = (ly + 1) * PX + (lx + 1);
 
@@ -1106,7 +1106,7 @@ sc_step_bulk_kernel(const float* __restrict__ src, float* __restrict__ dst, cons
     // consumers
     const int lx = tid % TX, ly = tid / TX;
     const int warp = tid / 32, lane = tid % 32;
-    const R rho0 = R(a.rho0), inv_rho0 = R(a.inv_rho0);
+    const R rho0 = par<R>(a.rho0, a.rho0f), inv_rho0 = par<R>(a.inv_rho0, a.inv_rho0f);
     const int my_slot = (ly + 1) * PX + (lx + 1);
     const int my_st = (ly + 1) * COLS + (lx + 4);
     int h_slot = -1, h_st = 0;
@@ -1248,7 +1248,7 @@ sc_step_tma_kernel(const __grid_constant__ CUtensorMap tmap, const float* __rest
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const long long n = a.n;
     const long long plane = (long long)nx * ny;
-    const R rho0 = R(a.rho0), inv_rho0 = R(a.inv_rho0);
+    const R rho0 = par<R>(a.rho0, a.rho0f), inv_rho0 = par<R>(a.inv_rho0, a.inv_rho0f);
     const int my_slot = (ly + 1) * PX + (lx + 1);
     const int my_st = ly * TX + lx;
     bool bad = false;

@@ -53,7 +53,7 @@ sc_step_mr_kernel(const typename Codec::S* __restrict__ src, typename Codec::S* 
     const long long yoff[3] = {(long long)ym * nx, (long long)gy * nx, (long long)yp * nx};
     const int xidx[3] = {xm, gx, xp};
 
-    const R rho0 = R(a.rho0), inv_rho0 = R(a.inv_rho0);
+    const R rho0 = par<R>(a.rho0, a.rho0f), inv_rho0 = par<R>(a.inv_rho0, a.inv_rho0f);
     const DevParams dev = a.dev;
     // G1 w(s) + G2 p(s) / 3 per shell s = |e|^2
     R coef[9];
@@ -97,10 +97,11 @@ sc_step_mr_kernel(const typename Codec::S* __restrict__ src, typename Codec::S* 
             });
             const R mpsi = -pl[2][my_slot];
             const R Fx = mpsi * sx, Fy = mpsi * sy, Fz = mpsi * sz;
-            if constexpr (COLL == COLL_SRT) collide_srt<R>(fc, Fx, Fy, Fz, R(a.tau), R(a.omega));
-            else if constexpr (COLL == COLL_MRT) collide_mrt<R>(fc, Fx, Fy, Fz, a.s);
-            else if constexpr (COLL == COLL_MRT_SPARSE) collide_mrt_sparse<R, false>(fc, Fx, Fy, Fz, a.s);
-            else collide_mrt_sparse<R, true>(fc, Fx, Fy, Fz, a.s);
+            if constexpr (COLL == COLL_SRT)
+                collide_srt<R>(fc, Fx, Fy, Fz, par<R>(a.tau, a.tauf), par<R>(a.omega, a.omegaf));
+            else if constexpr (COLL == COLL_MRT) collide_mrt<R>(fc, Fx, Fy, Fz, rates<R>(a));
+            else if constexpr (COLL == COLL_MRT_SPARSE) collide_mrt_sparse<R, false>(fc, Fx, Fy, Fz, rates<R>(a));
+            else collide_mrt_sparse<R, true>(fc, Fx, Fy, Fz, rates<R>(a));
             // Eq. LBE streaming: f_a(x + c_a, t + 1) = f*_a(x, t).
             const int zm = (z == 0) ? nz - 1 : z - 1, zn = (z + 1 == nz) ? 0 : z + 1;
             const long long zoff[3] = {(long long)zm * plane, zo, (long long)zn * plane};
