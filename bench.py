@@ -42,7 +42,7 @@ BYTES_PER_POP = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "f16l": 2, "bf16l": 2}
 EXTRA_BYTES_PER_CELL = {"f16l": 8, "bf16l": 8}
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_NAMES = {1: "sc_step_kernel", 2: "sc_step_async_kernel", 3: "sc_step_pipe_kernel", 4: "sc_step_bulk_kernel",
-                5: "sc_step_tma_kernel", 6: "sc_step_mr_kernel"}
+                5: "sc_step_tma_kernel", 6: "sc_step_mr_kernel", 7: "sc_step_pair16_kernel"}
 
 
 def parse_args():
@@ -64,13 +64,15 @@ def parse_args():
     ap.add_argument("--zchunk", type=int, default=0)
     ap.add_argument("--tile-y", type=int, default=0)
     ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 register-staged, 2 cp.async-staged, 3 pipelined, 4 bulk-copy, "
-                         "5 tensor-copy")
+                         "5 tensor-copy, 7 paired 16-bit")
     ap.add_argument("--e2e-steps", type=int, default=1000)
     ap.add_argument("--e2e-diag-every", type=int, default=50,
                     help="e2e: steps between diagnostics read back to the host (the paper's break-up runs "
                          "sample every t_cap/40, 63 steps for the R0 = 64 ligament)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="single form: skip the FP64 / 16-bit / batched / adjoint record beside the headline")
     ap.add_argument("--form", choices=["single", "batched", "adjoint", "precision", "paper", "calibrate", "multirange"],
                     default="single",
                     help="single: the sharp-interface ligament; batched: 64 uneven ligaments in one launch per "
@@ -260,6 +262,114 @@ def c_reference_mlups(w, args, slab, steps):
     return rho.size * steps / dt / 1e6, n, desc
 
 
+# ------------------------------------------------------------ other forms
+def measure_rate(storage, steps, warmup, R0=64.0, kR0=0.7, collision="srt", tau=1.0):
+    """Device time per step (CUDA events on the lattice's stream around
+    `steps` step launches) of the ligament R0, kR0 with `storage`
+    populations; returns GLUPS, ms per step, cells and the launch shape."""
+    import torch
+
+    from paper_1905_09554_gb300 import inputs, lbm
+    nx, ny, nz = inputs.ligament_box(R0, kR0)
+    forcing = "shift" if collision == "srt" else "guo"
+    rl, rv = inputs.COEXISTENCE[(forcing, -5.5, 1.0)]
+    rates = None
+    if collision == "mrt":
+        rates = [1.0] * 19
+        for k in (9, 11, 13, 14, 15):
+            rates[k] = 1.0 / tau
+    with lbm.Lattice(nx, ny, nz, G=-5.5, tau=tau, collision=collision, rates=rates, storage=storage) as L:
+        L.init_ligament(R0, 0.05, rl, rv)
+        L.step(warmup)
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        L.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        cfg = L.kernel_config()
+    cells = nx * ny * nz
+    return {"glups": cells / (ms / 1e3) / 1e9, "ms_per_step": ms, "cells": cells, "kernel": cfg}
+
+
+def breakup_run_to_pinch(storage, R0=16.0, kR0=0.7, collision="srt", tau=1.0, every=5, max_steps=20000):
+    """Run the ligament R0, kR0 (5% perturbation, G = -5.5) to its first
+    pinch-off, sampling the diagnostics every `every` steps; returns the
+    break-up time in steps (interpolated; None if none within max_steps)
+    and the density after 200 steps."""
+    from paper_1905_09554_gb300 import diagnostics as dg
+    from paper_1905_09554_gb300 import inputs, lbm
+    nx, ny, nz = inputs.ligament_box(R0, kR0)
+    forcing = "shift" if collision == "srt" else "guo"
+    rl, rv = inputs.COEXISTENCE[(forcing, -5.5, 1.0)]
+    with lbm.Lattice(nx, ny, nz, G=-5.5, tau=tau, collision=collision, storage=storage) as L:
+        L.init_ligament(R0, 0.05, rl, rv)
+        L.step(200)
+        rho200 = L.density()
+        ts, mins, t = [], [], 200
+        while t <= max_steps:
+            d = L.diag(rl, rv, raise_nonfinite=False)
+            ts.append(t)
+            mins.append(float(d["maxrho_z"].min()))
+            if mins[-1] < 0.5 * (rl + rv) or d["status"] != 0:
+                break
+            L.step(every)
+            t += every
+    return dg.breakup_time(ts, mins, rl, rv), rho200
+
+
+def measure_forms(device, clocks):
+    """The forms named beside the headline metric, each against the plain
+    FP64 single-ligament step: FP64, FP16 / FP16-local rates on the headline
+    box; FP32 / FP16-local / BF16-local accuracy over a break-up run
+    (R0 = 16); the batched form; the adjoint form.  About half a minute."""
+    peak = measured_hbm()[0]
+    forms = {"rates_workload": "ligament R0=64 kR0=0.7 box 256x256x575, G=-5.5, SRT tau=1 (device time, CUDA "
+                               "events around the step launches)",
+             "accuracy_workload": "ligament R0=16 kR0=0.7 box 64x64x144, G=-5.5, SRT tau=1, 5% perturbation, "
+                                  "run to the first pinch-off, diagnostics every 5 steps; errors against the "
+                                  "FP64 GPU run of the same case"}
+    f64 = measure_rate("f64", steps=20, warmup=3)
+    rec = step_record()
+    fpc = rec.get("fp64_flops_per_cell") if rec else None
+    pk, src = fp64_peak(device, clocks)
+    forms["f64"] = {"glups": f64["glups"], "ms_per_step": f64["ms_per_step"],
+                    "hbm_frac": 304 * f64["glups"] / peak,
+                    "fp64_pipe_frac": (fpc * f64["glups"] / 1e3 / pk) if fpc else None,
+                    "fp64_flops_per_cell": fpc, "fp64_peak_tflops": pk, "fp64_peak_source": src,
+                    "kernel": f64["kernel"]}
+    for st, bpc in (("f16l", 84), ("f16", 76), ("bf16l", 84)):
+        r = measure_rate(st, steps=100, warmup=5)
+        forms[st] = {"glups": r["glups"], "ms_per_step": r["ms_per_step"], "bytes_per_cell": bpc,
+                     "hbm_frac": bpc * r["glups"] / peak, "speedup_vs_f64": r["glups"] / f64["glups"],
+                     "kernel": r["kernel"]}
+    import numpy as np
+    tb64, rho64 = breakup_run_to_pinch("f64")
+    forms["f64"]["t_break_steps_R0_16"] = tb64
+    for st in ("f32", "f16l", "bf16l"):
+        tb, rho = breakup_run_to_pinch(st)
+        forms.setdefault(st, {})
+        forms[st]["t_break_steps_R0_16"] = tb
+        forms[st]["t_break_rel_err_vs_f64"] = abs(tb - tb64) / tb64 if tb and tb64 else None
+        forms[st]["max_abs_rho_err_200_vs_f64"] = float(np.abs(rho - rho64).max())
+    b = measure_batched(300, 10)
+    forms["batched"] = {"ligaments_per_s": b["ligaments_per_s"], "aggregate_glups": b["aggregate_mlups"] / 1e3,
+                        "hbm_frac": b["hbm_gbs"] / peak, "speedup_vs_f64": b["aggregate_mlups"] / 1e3 / f64["glups"],
+                        "cells": b["cells"], "tile_y": b["config"]["tile_y"], "zchunk": b["config"]["zchunk"],
+                        "workload": "64 ligaments R0 in {8,12,16}, kR0 ~ U[0.2,1.0) seed 0, FP32 SRT; ligaments/s "
+                                    "of 3000-step runs from 300 timed steps"}
+    adj = measure_adjoint()
+    a, d = adj["f32"], adj["f64"]
+    forms["adjoint"] = {"f32_adjoint_steps_per_s": adj["T"] / a["bwd_s"],
+                        "f64_adjoint_steps_per_s": adj["T"] / d["bwd_s"],
+                        "f32_forward_with_checkpoints_steps_per_s": adj["T"] / a["fwd_s"],
+                        "f32_vs_f64_gradient": adj["fp32_vs_fp64"],
+                        "workload": "64x64x180 ligament, neck energy at step 500, checkpoints every 23"}
+    return forms
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -417,14 +527,14 @@ def run_ours(args):
     kname = KERNEL_NAMES.get(L_info["kernel"], "sc_step_kernel")
     rec = step_record()
     if args.storage == "f64" and rec and rec.get("fp64_flops_per_cell"):
-        # FP64 is bound by the FP64 pipe: 152 SMs x 2 FP64 instructions per
-        # clock (ncu's peak_sustained) x 2.07 GHz x 2 flops per FMA.
+        # FP64 is bound by the FP64 pipe: SMs x 2 FP64 lanes per clock
+        # (ncu's peak_sustained) x SM clock x 2 flops per FMA.
         fpc = rec["fp64_flops_per_cell"]
         achieved = fpc * ncell / (kernel_ms / 1e3) / 1e12
-        peak_alu = 152 * 2 * 2.07e9 * 2 / 1e12
+        peak_alu, peak_src = fp64_peak(local, clocks)
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
                     "frac": achieved / peak_alu, "traffic": load_traffic(args, ncell, L_info),
-                    "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz x 2 flop (derived)",
+                    "peak_source": peak_src,
                     "kernel": kname, "fp64_flops_per_cell": fpc, "kernel_ms": kernel_ms,
                     "hbm_frac": bpc * ncell / (kernel_ms / 1e3) / 1e9 / peak}
     else:
@@ -443,6 +553,10 @@ def run_ours(args):
             cpu["openmp_c_reference"] = {"value": c_res[0], "unit": "MLUPS", "threads": c_res[1],
                                          "sample": c_res[2]}
 
+    forms = None
+    if not args.no_forms and world == 1:
+        forms = measure_forms(local, clocks)
+
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -455,11 +569,31 @@ def run_ours(args):
                          f"{19 * BYTES_PER_POP[args.storage] * ncell / 1e9:.2f} GB each)",
                    "mass_rel_drift": mass_drift},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        "gpu_launches": args.steps, "host": host_info(),
+        "gpu_launches": args.steps, "host": host_info(), "forms": forms,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def fp64_peak(device, clocks=None):
+    """FP64 pipe peak in TFLOP/s: the device's SM count x 2 FP64 lanes per SM
+    and clock (ncu's peak_sustained for the FP64 pipe on GB300) x the median
+    SM clock sampled under load (else the maximum clock) x 2 flops per FMA."""
+    import torch
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz")
+    src = "sampled median SM clock"
+    if not mhz:
+        try:
+            mhz = float(subprocess.run(["nvidia-smi", "-i", str(device), "--query-gpu=clocks.max.sm",
+                                        "--format=csv,noheader,nounits"], capture_output=True,
+                                       text=True, timeout=10).stdout.split()[0])
+            src = "maximum SM clock"
+        except Exception:  # noqa: BLE001
+            mhz, src = 2070.0, "nominal maximum SM clock"
+    peak = sms * 2 * mhz * 1e6 * 2 / 1e12
+    return peak, f"FP64 pipe: {sms} SMs x 2 lanes/clk x {mhz:.0f} MHz ({src}) x 2 flop (derived)"
 
 
 def step_record():
@@ -490,53 +624,64 @@ def load_traffic(args, ncell, info):
     return per * ncell if per is not None else None
 
 
-def run_batched(args):
+def measure_batched(steps, warmup, trial_steps=3):
     """64 independent ligaments (R0 in {8, 12, 16}, kR0 uniform on [0.2, 1.0)
     from seed 0, box 4R0 x 4R0 x round(2 pi R0 / kR0)), FP32 SRT tau = 1,
     G = -5.5, 3% perturbation, advanced together by one launch per step
     (pairs of steps from a CUDA graph) after the launch-shape autotuner.
-    `value` is ligaments/s: complete runs of --steps steps per second."""
+    Returns the device time of `steps` steps and the chosen configuration."""
     import torch
 
     from paper_1905_09554_gb300 import inputs, lbm
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     insts = inputs.batch_instances(64, seed=0)
     dims = [(d["nx"], d["ny"], d["nz"]) for d in insts]
     rl, rv = inputs.COEXISTENCE[("shift", -5.5, 1.0)]
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         B = lbm.Batch(dims, G=-5.5, tau=1.0, collision="srt", storage="f32", stream=stream.cuda_stream)
-        best = B.tune(trial_steps=3)
+        best = B.tune(trial_steps=trial_steps)
         for box, d in zip(B.boxes, insts):
             box.init_ligament(d["R0"], 0.03, rl, rv)
-        B.step(args.warmup)
+        B.step(warmup)
         cfg = B.config()
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         t0.record(stream)
-        B.step(args.steps)
+        B.step(steps)
         t1.record(stream)
         torch.cuda.synchronize()
         ms = t0.elapsed_time(t1)
         B.close()
     cells = cfg["cells"]
+    return {"ms": ms, "steps": steps, "cells": cells, "config": cfg, "tune": best,
+            "ligaments_per_s": 64.0 / (ms / 1e3 * 3000.0 / steps),
+            "aggregate_mlups": cells * steps / (ms / 1e3) / 1e6,
+            "hbm_gbs": 152 * cells / (ms / steps / 1e3) / 1e9}
+
+
+def run_batched(args):
+    """The batched form: `value` is ligaments/s, complete runs of 3000 steps
+    per second, measured over --steps steps."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    m = measure_batched(args.steps, args.warmup)
+    cfg = m["config"]
+    peak = measured_hbm()[0]
     line = {
         "metric": "batched ligaments/s (64 uneven ligaments, one launch per step)",
-        "value": None,
+        "value": m["ligaments_per_s"],
         "unit": "ligaments/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": m["ms"] / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "64 ligaments, R0 in {8,12,16}, kR0 ~ U[0.2,1.0) seed 0, boxes 4R0x4R0xround(2piR0/kR0), "
                                "G=-5.5, SRT tau=1, FP32, 3% perturbation",
-                   "cells": cells, "tile_y": cfg["tile_y"], "zchunk": cfg["zchunk"], "grid": cfg["grid"],
-                   "autotune_ms_per_step": best["ms_per_step"]},
-        "aggregate_mlups": cells * args.steps / (ms / 1e3) / 1e6,
-        "roofline": {"bound": "hbm", "achieved": 152 * cells / (ms / args.steps / 1e3) / 1e9,
-                     "peak": measured_hbm()[0], "unit": "GB/s"},
+                   "cells": m["cells"], "tile_y": cfg["tile_y"], "zchunk": cfg["zchunk"], "grid": cfg["grid"],
+                   "autotune_ms_per_step": m["tune"]["ms_per_step"]},
+        "aggregate_mlups": m["aggregate_mlups"],
+        "roofline": {"bound": "hbm", "achieved": m["hbm_gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": m["hbm_gbs"] / peak},
         "gpu_launches": args.steps,
     }
-    line["value"] = 64.0 / (ms / 1e3 * 3000.0 / args.steps)
-    line["roofline"]["frac"] = line["roofline"]["achieved"] / line["roofline"]["peak"]
     print(json.dumps(line), flush=True)
 
 
@@ -549,21 +694,19 @@ def golden_sigma(forcing):
         return None
 
 
-def run_adjoint(args):
-    """Gradient of the neck energy J = mean_z (R(z) - mean R)^2 at step 500 with
-    respect to the initial density, G and tau, for the 64 x 64 x 180 ligament
-    (R0 = 16, kR0 = 0.56, 5% perturbation plus N(0, 1e-3) per-cell noise from
-    seed 1), SRT tau = 1, G = -5.5, FP32 populations, checkpoints every 23
-    steps.  `value` is adjoint steps/s of the backward pass (which includes
-    recomputing each segment from its checkpoint); the FP64 gradient of the
-    same problem is the accuracy reference."""
+def measure_adjoint(T=500, every=23):
+    """Gradient of the neck energy J = mean_z (R(z) - mean R)^2 at step T with
+    respect to the initial density, G and tau, for the 64 x 64 x 180
+    ligament (R0 = 16, kR0 = 0.56, 5% perturbation plus N(0, 1e-3) per-cell
+    noise from seed 1), SRT tau = 1, G = -5.5, checkpoints every `every`
+    steps, with FP32 and with FP64 populations.  Returns per precision the
+    objective, the gradients and the forward / backward wall times."""
     import numpy as np
     import torch
 
     from paper_1905_09554_gb300 import inputs, lbm
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     nx, ny, nz = 64, 64, 180
-    R0, T, every = 16.0, 500, 23
+    R0 = 16.0
     rl, rv = inputs.COEXISTENCE[("shift", -5.5, 1.0)]
     rho0 = inputs.noisy_ligament_density(nx, ny, nz, R0, 0.05, rl, rv, 1e-3, seed=1)
 
@@ -587,6 +730,23 @@ def run_adjoint(args):
             t3 = time.perf_counter()
         out[storage] = dict(J=J, grad=grad, dG=gG, dtau=gT, fwd_s=t1 - t0, bwd_s=t3 - t2)
     a, b = out["f32"], out["f64"]
+    out["fp32_vs_fp64"] = {"dJ_dG_rel": abs(a["dG"] - b["dG"]) / abs(b["dG"]),
+                           "dJ_dtau_rel": abs(a["dtau"] - b["dtau"]) / abs(b["dtau"]),
+                           "dJ_drho0_maxabs_rel": float(np.abs(a["grad"] - b["grad"]).max()
+                                                        / np.abs(b["grad"]).max())}
+    out["cells"], out["T"], out["every"] = nx * ny * nz, T, every
+    return out
+
+
+def run_adjoint(args):
+    """The adjoint form (see measure_adjoint): `value` is adjoint steps/s of
+    the FP32 backward pass (which includes recomputing each segment from its
+    checkpoint); the FP64 gradient of the same problem is the accuracy
+    reference."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    out = measure_adjoint()
+    a, b, T = out["f32"], out["f64"], out["T"]
     line = {
         "metric": "adjoint steps/s (SRT, 64x64x180, 500 steps, checkpoints every 23)",
         "value": T / a["bwd_s"], "unit": "adjoint steps/s", "n_gpus": 1, "steps": T, "warmup": 0,
@@ -594,13 +754,11 @@ def run_adjoint(args):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "ligament 64x64x180, R0=16, kR0=0.56, 5% perturbation + N(0,1e-3) noise seed 1, "
                                "G=-5.5, SRT tau=1, objective: neck energy at step 500",
-                   "checkpoint_every": every, "cells": nx * ny * nz},
+                   "checkpoint_every": out["every"], "cells": out["cells"]},
         "forward_with_checkpoints_steps_per_s": T / a["fwd_s"],
         "fp64": {"adjoint_steps_per_s": T / b["bwd_s"], "dJ_dG": b["dG"], "dJ_dtau": b["dtau"], "J": b["J"]},
         "fp32": {"dJ_dG": a["dG"], "dJ_dtau": a["dtau"], "J": a["J"]},
-        "fp32_vs_fp64": {"dJ_dG_rel": abs(a["dG"] - b["dG"]) / abs(b["dG"]),
-                         "dJ_dtau_rel": abs(a["dtau"] - b["dtau"]) / abs(b["dtau"]),
-                         "dJ_drho0_maxabs_rel": float(np.abs(a["grad"] - b["grad"]).max() / np.abs(b["grad"]).max())},
+        "fp32_vs_fp64": out["fp32_vs_fp64"],
     }
     print(json.dumps(line), flush=True)
 

@@ -82,7 +82,7 @@ typedef struct {
                              initialised, and by every step to the density of the
                              cell before the step (so f(t+1) is stored relative to
                              rho(t), which differs from rho(t+1) by O(|div j|)).
-                             Local-reference storage runs step kernel 1 or 3 and
+                             Local-reference storage runs step kernel 1, 3 or 7 and
                              is not accepted by batches, the adjoint or
                              lbm_diag_noalloc.                                        */
     double dev_scale;     /* deviation storage scale (> 0)                          */
@@ -93,12 +93,15 @@ typedef struct {
                              allocates (and frees them in lbm_destroy).            */
     int zchunk;           /* step kernel: z planes per work item; 0 = auto (at most
                              32, and at most 24 MiB of one population's planes
-                             on 32x16 tiles)                                        */
+                             on 32x16 tiles; 8 when one population's plane is
+                             1.5 MiB or more)                                       */
     int tile_y;           /* step kernel: tile height (4, 8 or 16); 0 = auto: 16
                              for FP32 SRT and unit-rate MRT, 8 for other FP32
-                             MRT, 4 otherwise                                       */
-    int kernel;           /* step kernel variant: 0 = auto (3 for FP32, and for
-                             the 16-bit formats when nx is even; else 1),
+                             MRT and for kernel 7, 4 otherwise                      */
+    int kernel;           /* step kernel variant: 0 = auto (3 for FP32 and the
+                             local-reference formats, 7 for the global-reference
+                             16-bit formats, when nx is even for 16-bit storage;
+                             else 1),
                              1 = register-staged,
                              2 = cp.async-staged persistent, 3 = pipelined
                              persistent (2: FP64/FP32 storage; 3: also the
@@ -108,7 +111,13 @@ typedef struct {
                              nx % 32 == 0, ny % tile_y == 0; steps on buffers
                              other than the two copies, e.g. the adjoint's
                              recomputation, run kernel 3),
-                             6 = two-belt force (chosen when G2 != 0)               */
+                             6 = two-belt force (chosen when G2 != 0),
+                             7 = paired 16-bit pipeline: two cells per thread
+                             along x, 64-cell tile rows, shifted pushes as
+                             aligned 32-bit words through warp shuffles (16-bit
+                             formats, nx even; the auto choice for the
+                             global-reference ones).  Kernels 3 and 7 need
+                             nx*ny*nz < 2^32 (auto then falls back to 1).    */
     int test_stall;       /* test only: with kernel 4 the copy warp issues nothing,
                              so every bounded wait times out (about 1 s) and the
                              next lbm_diag / lbm_moments / lbm_get_populations

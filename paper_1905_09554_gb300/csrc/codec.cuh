@@ -60,9 +60,11 @@ struct CodecF16Dev {
     template <int q>
     __device__ __forceinline__ static R load(const S* p, const DevParams& d) { return decode<q>(__ldg(p), d); }
     template <int q>
-    __device__ __forceinline__ static void store(S* p, R v, const DevParams& d) {
-        *p = __float2half_rn((v - float(wq(q)) * d.rho_ref) * d.scale);
+    __device__ __forceinline__ static S encode(R v, const DevParams& d) {
+        return __float2half_rn((v - float(wq(q)) * d.rho_ref) * d.scale);
     }
+    template <int q>
+    __device__ __forceinline__ static void store(S* p, R v, const DevParams& d) { *p = encode<q>(v, d); }
 };
 
 struct CodecBF16Dev {
@@ -77,9 +79,11 @@ struct CodecBF16Dev {
     template <int q>
     __device__ __forceinline__ static R load(const S* p, const DevParams& d) { return decode<q>(__ldg(p), d); }
     template <int q>
-    __device__ __forceinline__ static void store(S* p, R v, const DevParams& d) {
-        *p = __float2bfloat16_rn((v - float(wq(q)) * d.rho_ref) * d.scale);
+    __device__ __forceinline__ static S encode(R v, const DevParams& d) {
+        return __float2bfloat16_rn((v - float(wq(q)) * d.rho_ref) * d.scale);
     }
+    template <int q>
+    __device__ __forceinline__ static void store(S* p, R v, const DevParams& d) { *p = encode<q>(v, d); }
 };
 
 
@@ -112,8 +116,12 @@ struct CodecLocal16 {
         return decode_ref<q>(__ldg(p), ref, d);
     }
     template <int q>
+    __device__ __forceinline__ static S encode_ref(R v, float ref, const DevParams& d) {
+        return from_f((v - float(wq(q)) * ref) * d.scale);
+    }
+    template <int q>
     __device__ __forceinline__ static void store_ref(S* p, R v, float ref, const DevParams& d) {
-        *p = from_f((v - float(wq(q)) * ref) * d.scale);
+        *p = encode_ref<q>(v, ref, d);
     }
     __device__ __forceinline__ static double decode_rt(const S* p, float w, float ref, const DevParams& d) {
         return double(w * ref + to_f(*p) * d.inv_scale);

@@ -332,7 +332,7 @@ StepLaunch step_launch(const lbm_ctx* c) {
 int prepare_async(lbm_ctx* c) {
     const int st = c->p.storage;
     // 16-bit storage: the pipelined kernel only, with nx even
-    const bool word16 = st >= LBM_F16_DEV && c->kernel == 3 && c->p.nx % 2 == 0;
+    const bool word16 = st >= LBM_F16_DEV && (c->kernel == 3 || c->kernel == 7) && c->p.nx % 2 == 0;
     if (st != LBM_F64 && st != LBM_F32 && !word16) return 0;
     return step_kernels(st, c->coll).prepare(step_launch(c));
 }
@@ -518,8 +518,10 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     if (p->storage < LBM_F64 || p->storage > LBM_BF16_LOCAL) return create_fail(LBM_EINVAL, "lbm_create: unknown storage");
     if (p->storage >= LBM_F16_DEV && (!(p->dev_scale > 0) || !std::isfinite(p->rho_ref)))
         return create_fail(LBM_EINVAL, "lbm_create: deviation storage needs dev_scale > 0 and finite rho_ref");
-    if (p->storage >= LBM_F16_LOCAL && (p->kernel == 2 || p->kernel >= 4))
-        return create_fail(LBM_EINVAL, "lbm_create: local-reference storage runs kernel 1 or 3");
+    if (p->storage >= LBM_F16_LOCAL && (p->kernel == 2 || (p->kernel >= 4 && p->kernel != 7)))
+        return create_fail(LBM_EINVAL, "lbm_create: local-reference storage runs kernel 1, 3 or 7");
+    if (p->kernel == 7 && (p->storage < LBM_F16_DEV || p->nx % 2 != 0))
+        return create_fail(LBM_EINVAL, "lbm_create: kernel 7 needs 16-bit storage and nx even");
     if (p->collision == LBM_MRT_GUO && p->has_rates) {
         for (int k = 0; k < Q; ++k)
             if (!(p->s[k] > 0.0 && p->s[k] < 2.0))
@@ -646,12 +648,17 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     // register-staged kernel on 32x4 tiles.
     const bool wide_ok = p->storage == LBM_F32 || p->storage == LBM_F64;
     const bool pipe_default = p->storage == LBM_F32 || (p->storage >= LBM_F16_DEV && p->nx % 2 == 0);
+    // the global-reference 16-bit formats run the paired kernel on 64x8 tiles
+    // (FP16 SRT 35.7 GLUPS against 32.7 for kernel 3 on 32x4 tiles at
+    // 256x256x575); the local-reference ones stay on kernel 3 (30.9 against 29.2)
+    const bool pair_default = (p->storage == LBM_F16_DEV || p->storage == LBM_BF16_DEV) && p->nx % 2 == 0;
     const int coll = c->coll;
     const bool wide = wide_ok && (coll == COLL_SRT || coll == COLL_MRT_UNIT) &&
                       (p->kernel == 3 || (p->kernel == 0 && pipe_default));
     const bool mrt8 = p->storage == LBM_F32 && (coll == COLL_MRT || coll == COLL_MRT_SPARSE) &&
                       (p->kernel == 3 || (p->kernel == 0 && pipe_default));
-    c->tile_y = p->tile_y ? p->tile_y : ((wide || p->kernel == 5) ? 16 : (mrt8 ? 8 : 4));
+    const bool pair = p->kernel == 7 || (p->kernel == 0 && pair_default);
+    c->tile_y = p->tile_y ? p->tile_y : ((wide || p->kernel == 5) ? 16 : ((mrt8 || pair) ? 8 : 4));
     if (p->G2 != 0.0) c->tile_y = p->tile_y ? p->tile_y : 8;  // the two-belt kernel
     if (p->kernel == 4 && (p->storage != LBM_F32 || p->nx % 4 != 0)) {
         snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel 4 needs FP32 storage and nx %% 4 == 0");
@@ -664,14 +671,21 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
         lbm_destroy(c);
         return LBM_EINVAL;
     }
-    if (p->kernel < 0 || p->kernel > 6) {
-        snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel must be 0 .. 6");
+    if (p->kernel < 0 || p->kernel > 7) {
+        snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel must be 0 .. 7");
+        lbm_destroy(c);
+        return LBM_EINVAL;
+    }
+    // kernels 3 and 7 address cells with 32-bit offsets within a population
+    const bool off32 = n <= 0xffffffffLL;
+    if (!off32 && (p->kernel == 3 || p->kernel == 7)) {
+        snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel %d needs nx*ny*nz < 2^32", p->kernel);
         lbm_destroy(c);
         return LBM_EINVAL;
     }
     c->kernel = p->G2 != 0.0 ? 6 : 1;
-    if (p->G2 == 0.0 && p->kernel != 1 && !(p->kernel == 0 && !pipe_default)) {
-        c->kernel = p->kernel == 0 ? 3 : p->kernel;
+    if (p->G2 == 0.0 && p->kernel != 1 && !(p->kernel == 0 && (!pipe_default || !off32))) {
+        c->kernel = p->kernel == 0 ? (pair_default ? 7 : 3) : p->kernel;
         const int per_sm = prepare_async(c);
         if (per_sm > 0) {
             c->grid = per_sm * c->num_sms;
@@ -702,7 +716,8 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
         }
         c->grid3 = per3 * c->num_sms;
     }
-    const int tiles_x = (p->nx + 31) / 32, tiles_y = (p->ny + c->tile_y - 1) / c->tile_y;
+    const int tile_w = c->kernel == 7 ? 64 : 32;  // kernel 7: two cells per thread along x
+    const int tiles_x = (p->nx + tile_w - 1) / tile_w, tiles_y = (p->ny + c->tile_y - 1) / c->tile_y;
     if (p->zchunk) {
         c->zchunk = p->zchunk < p->nz ? p->zchunk : p->nz;
     } else if (c->kernel >= 2 && c->kernel != 6) {
@@ -723,6 +738,10 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
             const long long plane_bytes = (long long)p->nx * p->ny * (long long)c->elem;
             zmax = (24LL << 20) / (plane_bytes > 0 ? plane_bytes : 1);
             zmax = zmax < 16 ? 16 : (zmax > 32 ? 32 : zmax);
+            // planes of a population of 1.5 MiB and more (672^2 FP32, the
+            // paper's R0 = 98 box): 8 planes, measured 28.7 GLUPS against
+            // 27.7 / 20.0 / 25.0 for 6 / 12 / 16
+            if (plane_bytes >= (3LL << 19)) zmax = 8;
         }
         if (zc > zmax) zc = zmax;
         if (zc < 8) zc = 8;

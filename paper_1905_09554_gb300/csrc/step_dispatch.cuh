@@ -5,6 +5,7 @@
 #include "step_args.h"
 #include "step_kernel.cuh"
 #include "step_multirange.cuh"
+#include "step_pair16.cuh"
 
 namespace lbm {
 
@@ -35,10 +36,19 @@ cudaError_t launch_step_t(const StepLaunch& c, const void* src, void* dst) {
             }
         }
     }
+    if constexpr (sizeof(typename Codec::S) == 2) {  // 16-bit formats, nx even (checked by the host)
+        if (c.kernel == 7) {
+            sc_step_pair16_kernel<Codec, COLL, TY, unsigned><<<c.grid, 32 * TY, Pair16Layout<Codec, TY>::bytes,
+                                                               c.stream>>>(
+                static_cast<const typename Codec::S*>(src), static_cast<typename Codec::S*>(dst), a);
+            return cudaGetLastError();
+        }
+    }
+    if (c.kernel == 7) return cudaErrorNotSupported;
     {  // every storage type (16-bit: nx even, checked by the host)
         if (c.kernel == 3) {
             const size_t sm = PipeLayout<Codec, TX, TY>::bytes;
-            sc_step_pipe_kernel<Codec, COLL, TX, TY, long long><<<c.grid, TX * TY, sm, c.stream>>>(
+            sc_step_pipe_kernel<Codec, COLL, TX, TY, unsigned><<<c.grid, TX * TY, sm, c.stream>>>(
                 static_cast<const typename Codec::S*>(src), static_cast<typename Codec::S*>(dst), a, BatchArgs{});
             return cudaGetLastError();
         }
@@ -80,10 +90,21 @@ int prepare_async_t(const StepLaunch& c) {
             return e == cudaSuccess ? per_sm : -int(e);
         }
     }
+    if constexpr (sizeof(typename Codec::S) == 2) {
+        if (c.kernel == 7) {
+            using Lay = Pair16Layout<Codec, TY>;
+            auto kern = sc_step_pair16_kernel<Codec, COLL, TY, unsigned>;
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes);
+            int per_sm = 0;
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Lay::NT, Lay::bytes);
+            return e == cudaSuccess ? per_sm : -int(e);
+        }
+    }
+    if (c.kernel == 7) return 0;
     {  // every storage type (16-bit: nx even, checked by the host)
         if (c.kernel == 3) {
             using Lay = PipeLayout<Codec, TX, TY>;
-            auto kern = sc_step_pipe_kernel<Codec, COLL, TX, TY, long long>;
+            auto kern = sc_step_pipe_kernel<Codec, COLL, TX, TY, unsigned>;
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes);
             int per_sm = 0;
             if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, Lay::bytes);

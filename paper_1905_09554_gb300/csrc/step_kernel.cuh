@@ -41,6 +41,15 @@ __device__ __forceinline__ float psi_of<float>(float rho, float rho0, float inv_
     return rho0 * (1.0f - expf(-rho * inv_rho0));
 }
 
+// Population q of the field starting at p (population stride n elements).
+// The 64-bit product comes from kernel parameters only, so with 32-bit cell
+// offsets (I = unsigned) an access costs the cell offset's 32-bit arithmetic
+// and one widening add.
+template <class S, class I>
+__device__ __forceinline__ S* pop_at(S* p, int q, I n) {
+    return p + (long long)q * (long long)n;
+}
+
 __device__ __forceinline__ int wrap_index(int i, int n) {
     i %= n;
     return i < 0 ? i + n : i;
@@ -338,9 +347,9 @@ __device__ __forceinline__ void update_cell(typename Codec::R (&fc)[Q], const ty
         if constexpr (Codec::kLocal) {
             // deviation from the rest equilibrium at the destination's density
             const float ref = rho_pl[cz(q) + 1][slot + cx(q) + cy(q) * PX];
-            Codec::template store_ref<q>(dst + (I(q) * n + idx), fc[q], ref, a.dev);
+            Codec::template store_ref<q>(pop_at(dst, q, n) + idx, fc[q], ref, a.dev);
         } else {
-            Codec::template store<q>(dst + (I(q) * n + idx), fc[q], a.dev);
+            Codec::template store<q>(pop_at(dst, q, n) + idx, fc[q], a.dev);
         }
     });
 }
@@ -784,11 +793,11 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src_all, typename Code
         auto slot_of = [&](int z) { return (z - zs + 1) & (L::NSLOT - 1); };
         auto issue_halo = [&](int z) {
             if (h_slot >= 0) {
-                const S* base = src + (I(wrapz(z)) * plane + h_xy - hpar);
+                const I off = I(wrapz(z)) * plane + h_xy - I(hpar);
                 HS* st = hstage + stage_of(z) * (Q * NH);
                 static_for<0, Q>([&](auto qc) {
                     constexpr int q = decltype(qc)::value;
-                    async_copy::copy<sizeof(HS)>(st + q * NH + h, base + I(q) * n);
+                    async_copy::copy<sizeof(HS)>(st + q * NH + h, pop_at(src, q, n) + off);
                 });
                 if constexpr (LOCAL)
                     async_copy::copy<4>(rstage + stage_of(z) * NH + h, a.ref_src + (I(wrapz(z)) * plane + h_xy));
@@ -819,17 +828,17 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src_all, typename Code
             }
         };
         auto load_plane = [&](R (&f)[Q], int z) {
-            const S* base = src + (I(wrapz(z)) * plane + my_xy);
+            const I off = I(wrapz(z)) * plane + my_xy;
             if constexpr (LOCAL) {
-                const float ref = __ldg(a.ref_src + (I(wrapz(z)) * plane + my_xy));
+                const float ref = __ldg(a.ref_src + off);
                 static_for<0, Q>([&](auto qc) {
                     constexpr int q = decltype(qc)::value;
-                    f[q] = Codec::template load_ref<q>(base + I(q) * n, ref, dev);
+                    f[q] = Codec::template load_ref<q>(pop_at(src, q, n) + off, ref, dev);
                 });
             } else {
                 static_for<0, Q>([&](auto qc) {
                     constexpr int q = decltype(qc)::value;
-                    f[q] = Codec::template load<q>(base + I(q) * n, dev);
+                    f[q] = Codec::template load<q>(pop_at(src, q, n) + off, dev);
                 });
             }
         };
@@ -878,10 +887,10 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src_all, typename Code
             auto body16 = [&](R (&fc)[Q], int z) {
                 const bool more = z + 2 <= ze;
                 if (more) {
-                    const S* base = src + (I(wrapz(z + 2)) * plane + my_xy);
+                    const I off = I(wrapz(z + 2)) * plane + my_xy;
                     static_for<0, Q>([&](auto qc) {
                         constexpr int q = decltype(qc)::value;
-                        fr[q] = __ldg(base + I(q) * n);
+                        fr[q] = __ldg(pop_at(src, q, n) + off);
                     });
                     if constexpr (LOCAL) fref = __ldg(a.ref_src + (I(wrapz(z + 2)) * plane + my_xy));
                     issue_halo(z + 2);

@@ -241,6 +241,30 @@ def test_pipelined_kernel_with_16_bit_storage_is_bit_identical(coll, storage):
                 assert np.array_equal(f, ref), (shape, tile_y, zchunk)
 
 
+@pytest.mark.parametrize("storage", ["f16", "bf16", "f16l", "bf16l"])
+@pytest.mark.parametrize("coll", ["srt", "mrt"])
+def test_paired_16_bit_kernel_is_bit_identical(coll, storage):
+    """Kernel 7 (two cells per thread, 64-cell tile rows, shifted pushes
+    through warp shuffles and 16-bit edge stores) against the register-staged
+    kernel: nx = 130 ends in a tile with one pair, nx = 40 is a single
+    partial tile, nx = 2 a single pair whose x neighbours are itself and its
+    twin, nx = 64 one full tile with rows past ny."""
+    for shape in ((130, 12, 23), (40, 12, 23), (2, 5, 7), (64, 9, 5)):
+        rho = inputs.noisy_ligament_density(*shape, 3.0, 0.1, RL, RV, 1e-3, seed=6)
+        ref, _, _ = gpu_run(rho, 10, storage, coll=coll, tau=0.8, kernel=1)
+        for tile_y in (4, 8, 16):
+            for zchunk in (1, 5, 23):
+                f, _, _ = gpu_run(rho, 10, storage, coll=coll, tau=0.8, kernel=7, tile_y=tile_y, zchunk=zchunk)
+                assert np.array_equal(f, ref), (shape, tile_y, zchunk)
+
+
+def test_paired_kernel_rejects_other_layouts():
+    with pytest.raises(lbm.LbmError, match="LBM_EINVAL"):
+        lbm.Lattice(9, 8, 8, storage="f16", kernel=7)  # nx odd
+    with pytest.raises(lbm.LbmError, match="LBM_EINVAL"):
+        lbm.Lattice(8, 8, 8, storage="f32", kernel=7)
+
+
 def test_staged_kernels_reject_unsupported_16_bit_layouts():
     with pytest.raises(lbm.LbmError, match="LBM_EINVAL"):
         lbm.Lattice(8, 8, 8, storage="f16", kernel=2)

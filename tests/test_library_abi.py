@@ -78,7 +78,7 @@ def test_create_rejects_bad_mrt_rates(lib):
     assert st == lbm.LBM_EINVAL and "rates" in lbm.lbm_last_error(None)
 
 
-def test_local_reference_storage_runs_kernels_1_and_3_only(lib):
+def test_local_reference_storage_runs_kernels_1_3_and_7_only(lib):
     for storage in (lbm.LBM_F16_LOCAL, lbm.LBM_BF16_LOCAL):
         p = lbm.lbm_params_default()
         p.storage = storage
@@ -86,7 +86,16 @@ def test_local_reference_storage_runs_kernels_1_and_3_only(lib):
             p.kernel = kernel
             st, ctx = lbm.lbm_create(p)
             assert st == lbm.LBM_EINVAL and not ctx.value
-            assert "kernel 1 or 3" in lbm.lbm_last_error(None)
+            assert "kernel 1, 3 or 7" in lbm.lbm_last_error(None)
+
+
+def test_paired_kernel_needs_16_bit_storage_and_even_nx(lib):
+    for storage, nx in ((lbm.LBM_F32, 32), (lbm.LBM_F64, 32), (lbm.LBM_F16_DEV, 33)):
+        p = lbm.lbm_params_default()
+        p.storage, p.nx, p.kernel = storage, nx, 7
+        st, ctx = lbm.lbm_create(p)
+        assert st == lbm.LBM_EINVAL and not ctx.value
+        assert "kernel 7 needs 16-bit storage and nx even" in lbm.lbm_last_error(None)
 
 
 def test_two_belt_force_parameters_are_validated_before_device_work(lib):
