@@ -253,7 +253,8 @@ long long lbm_device_bytes(const lbm_ctx *ctx);
 
 /* Launch configuration the context chose for the step kernel: variant
  * (1 register-staged, 2 cp.async-staged, 3 pipelined, 4 bulk-copy, 5 tensor
- * copy, 6 two-belt force), tile height, z planes per work item and grid size
+ * copy, 6 two-belt force, 7 paired 16-bit), tile height, z planes per work
+ * item and grid size
  * (blocks).  Any pointer may be NULL. */
 lbm_status lbm_kernel_config(const lbm_ctx *ctx, int *kernel, int *tile_y,
                              int *zchunk, int *grid);
@@ -273,7 +274,7 @@ long long lbm_params_sizeof(void);
  * n >= 1 steps and keep every `every`-th state (t = 0, every, 2 every, ...) as
  * a checkpoint in device memory owned by the context; the state ends at
  * t = n.  Checkpoint memory: ceil(n/every) + every states.  Collision must be
- * LBM_SRT_SHIFT and G2 zero (else LBM_EUNSUPPORTED). */
+ * LBM_SRT_SHIFT, G2 zero and nx*ny*nz < 2^32 (else LBM_EUNSUPPORTED). */
 lbm_status lbm_adjoint_forward(lbm_ctx *ctx, const double *rho0, int on_device,
                                long n, int every);
 
@@ -281,7 +282,9 @@ lbm_status lbm_adjoint_forward(lbm_ctx *ctx, const double *rho0, int on_device,
  * discrete adjoint back to t = 0, recomputing each segment's states from its
  * checkpoint, and return dJ/drho0 (float64 field, host or device; may be
  * NULL), dJ/dG and dJ/dtau (host doubles; may be NULL).  Synchronises the
- * context's stream. */
+ * context's stream.  Working memory besides the checkpoints: two adjoint
+ * states, `every` psi fields (the recomputation stores psi of each state it
+ * steps from, with step kernels 1, 3 and 5) and six more fields. */
 lbm_status lbm_adjoint_backward(lbm_ctx *ctx, const double *dJdrho,
                                 int in_on_device, double *dJdrho0,
                                 int out_on_device, double *dJdG,

@@ -14,6 +14,7 @@ struct AdjointArgs {
 };
 
 int adjoint_threads();
+int adjoint_rows_per_block();  // the step kernels walk x rows, this many per block
 // The adjoint field is kept as lam_a(x) + gr(x): the force's contribution to
 // dJ/drho is the same for every population, so it is stored once per cell
 // (gr, n values) instead of being added to the 19 populations.
@@ -22,10 +23,13 @@ int adjoint_threads();
 // forward state f; this step's dJ/dG and dJ/dtau are added to the per-block
 // running sums in `partials` (2 * grid doubles, zeroed before the first
 // step), which adjoint_reduce adds into acc[0..1] once after the last step.
-// psi (n) and gF (3n) are scratch; acc is not touched here.
-cudaError_t adjoint_step(const AdjointArgs& a, bool f64, const void* f, void* psi, const void* lam_next,
-                         const void* gr_next, void* lam_out, void* gr_out, void* gF, double* partials, double* acc,
-                         cudaStream_t st);
+// psi (n) and gF (4n: psi gF and S.gF, see adj_collide_kernel) are scratch;
+// acc is not touched here.  Needs nx*ny*nz < 2^32 (32-bit cell indices).
+// psi_ready: psi already holds psi of f (the step kernel wrote it during the
+// recomputation); otherwise it is computed first.
+cudaError_t adjoint_step(const AdjointArgs& a, bool f64, const void* f, void* psi, bool psi_ready,
+                         const void* lam_next, const void* gr_next, void* lam_out, void* gr_out, void* gF,
+                         double* partials, double* acc, cudaStream_t st);
 cudaError_t adjoint_reduce(const AdjointArgs& a, const double* partials, double* acc, cudaStream_t st);
 // lam_a = dJ/drho (every a), gr = 0.
 cudaError_t adjoint_seed(const AdjointArgs& a, bool f64, const double* dJdrho, void* lam, void* gr, cudaStream_t st);

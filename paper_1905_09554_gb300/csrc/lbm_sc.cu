@@ -57,12 +57,12 @@ struct lbm_ctx {
         void* seg = nullptr;          // recomputed states of one segment, `every` states
         void* lam[2] = {nullptr, nullptr};
         void* gr[2] = {nullptr, nullptr};  // the force term of lam, one value per cell
-        void* psi = nullptr;
-        void* gF = nullptr;
+        void* psi = nullptr;          // psi of each state of a segment, `every` fields
+        void* gF = nullptr;           // psi gF and S.gF of the reverse step, 4 fields
         double* partials = nullptr;   // 2 per block
         double* acc = nullptr;        // dJ/dG, dJ/dtau
         double* io = nullptr;         // host <-> device staging of one field
-        size_t cp_bytes = 0, seg_bytes = 0;
+        size_t cp_bytes = 0, seg_bytes = 0, psi_bytes = 0;
         long T = -1;                  // steps of the recorded forward run
         int every = 0, ncp = 0;
     } adj;
@@ -337,8 +337,9 @@ int prepare_async(lbm_ctx* c) {
     return step_kernels(st, c->coll).prepare(step_launch(c));
 }
 
-cudaError_t launch_step(const lbm_ctx* c, const void* src, void* dst) {
+cudaError_t launch_step(const lbm_ctx* c, const void* src, void* dst, void* psi_out = nullptr) {
     StepLaunch l = step_launch(c);
+    l.args.psi_out = psi_out;
     if (c->kernel == 5) {
         const int idx = src == c->f[0] ? 0 : (src == c->f[1] ? 1 : -1);
         if (idx >= 0) {
@@ -1382,7 +1383,8 @@ AdjointArgs adjoint_args(const lbm_ctx* c) {
     a.tauf = float(a.tau);
     a.omegaf = float(a.omega);
     a.rho0f = float(a.rho0);
-    const long long want = (c->n + adjoint_threads() - 1) / adjoint_threads();
+    const long long rows = (long long)c->p.ny * c->p.nz;
+    const long long want = (rows + adjoint_rows_per_block() - 1) / adjoint_rows_per_block();
     const long long cap = 8LL * c->num_sms;
     a.grid = int(want < cap ? (want < 1 ? 1 : want) : cap);
     return a;
@@ -1409,6 +1411,7 @@ lbm_status lbm_adjoint_forward(lbm_ctx* c, const double* rho0, int on_device, lo
     if (c->p.G2 != 0.0)
         return c->fail(LBM_EUNSUPPORTED, "lbm_adjoint_forward: the adjoint covers the single-belt force only");
     if (!rho0 || nsteps < 1 || every < 1) return c->fail(LBM_EINVAL, "lbm_adjoint_forward: need rho0, n >= 1, every >= 1");
+    if (c->n > 0xffffffffLL) return c->fail(LBM_EUNSUPPORTED, "lbm_adjoint_forward: needs nx*ny*nz < 2^32");
     auto& A = c->adj;
     const size_t state = (size_t)Q * (size_t)c->n * c->elem;
     const int ncp = int((nsteps + every - 1) / every);
@@ -1467,8 +1470,22 @@ lbm_status lbm_adjoint_backward(lbm_ctx* c, const double* dJdrho, int in_on_devi
         st = adj_alloc(c, p, (size_t)c->n * c->elem);
         if (st != LBM_OK) return st;
     }
-    if ((st = adj_alloc(c, &A.psi, (size_t)c->n * c->elem)) != LBM_OK) return st;
-    if ((st = adj_alloc(c, &A.gF, 3 * (size_t)c->n * c->elem)) != LBM_OK) return st;
+    // psi of every state of a segment: written by the step kernel during the
+    // recomputation where it supports that (kernels 1 and 3, and 5 whose
+    // recomputation runs kernel 3), else computed by the reverse step
+    const bool psi_fused = c->kernel == 1 || c->kernel == 3 || c->kernel == 5;
+    const size_t psi_bytes = (size_t)c->n * c->elem;
+    if (A.psi && A.psi_bytes < (size_t)A.every * psi_bytes) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(A.psi);
+        c->own_bytes -= (long long)A.psi_bytes;
+        A.psi = nullptr;
+    }
+    if (!A.psi) {
+        if ((st = adj_alloc(c, &A.psi, (size_t)A.every * psi_bytes)) != LBM_OK) return st;
+        A.psi_bytes = (size_t)A.every * psi_bytes;
+    }
+    if ((st = adj_alloc(c, &A.gF, 4 * (size_t)c->n * c->elem)) != LBM_OK) return st;
     if ((st = adj_alloc(c, reinterpret_cast<void**>(&A.partials), sizeof(double) * 2 * (size_t)a.grid)) != LBM_OK)
         return st;
     if ((st = adj_alloc(c, reinterpret_cast<void**>(&A.acc), sizeof(double) * 2)) != LBM_OK) return st;
@@ -1491,13 +1508,18 @@ lbm_status lbm_adjoint_backward(lbm_ctx* c, const double* dJdrho, int in_on_devi
         char* seg = static_cast<char*>(A.seg);
         LBM_CUDA(c, cudaMemcpyAsync(seg, static_cast<char*>(A.cp) + (size_t)k * state, state,
                                     cudaMemcpyDeviceToDevice, c->stream));
+        char* psi = static_cast<char*>(A.psi);
         for (long t = t0; t + 1 < t1; ++t) {
-            cudaError_t e = launch_step(c, seg + (size_t)(t - t0) * state, seg + (size_t)(t - t0 + 1) * state);
+            cudaError_t e = launch_step(c, seg + (size_t)(t - t0) * state, seg + (size_t)(t - t0 + 1) * state,
+                                        psi_fused ? psi + (size_t)(t - t0) * psi_bytes : nullptr);
             if (e != cudaSuccess) return c->fail(LBM_ECUDA, "adjoint recompute: %s", cudaGetErrorString(e));
         }
         for (long t = t1 - 1; t >= t0; --t) {
-            cudaError_t e = adjoint_step(a, f64, seg + (size_t)(t - t0) * state, A.psi, A.lam[cur], A.gr[cur],
-                                         A.lam[cur ^ 1], A.gr[cur ^ 1], A.gF, A.partials, A.acc, c->stream);
+            // the segment's last state has no recomputed step after it
+            const bool ready = psi_fused && t + 1 < t1;
+            cudaError_t e = adjoint_step(a, f64, seg + (size_t)(t - t0) * state, psi + (size_t)(t - t0) * psi_bytes,
+                                         ready, A.lam[cur], A.gr[cur], A.lam[cur ^ 1], A.gr[cur ^ 1], A.gF,
+                                         A.partials, A.acc, c->stream);
             if (e != cudaSuccess) return c->fail(LBM_ECUDA, "adjoint step: %s", cudaGetErrorString(e));
             cur ^= 1;
         }

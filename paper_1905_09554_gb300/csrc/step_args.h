@@ -35,6 +35,10 @@ struct StepArgs {
     const float* ref_src; // local-reference storage: density field of the source copy
     float* ref_dst;       // ... and of the destination copy
     int test_stall;       // failure test of the bounded waits (bulk kernel)
+    // Optional (kernels 1 and 3): psi of the input state, one value per cell
+    // in the arithmetic type (the adjoint's recomputation keeps it for the
+    // reverse step); nullptr normally.
+    void* psi_out;
 };
 
 // MRT rates in the arithmetic type R (see par() in lattice.cuh).

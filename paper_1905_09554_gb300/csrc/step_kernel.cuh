@@ -30,6 +30,10 @@
 
 namespace lbm {
 
+// psi = rho0 (1 - exp(-rho/rho0)).  Float arithmetic uses the hardware
+// exponential (__expf, a few ulp for the densities of a two-phase state,
+// |rho/rho0| < 4) instead of the correctly rounded expf, whose range
+// reduction costs about eight more instructions per call.
 template <class R>
 __device__ __forceinline__ R psi_of(R rho, R rho0, R inv_rho0);
 template <>
@@ -38,7 +42,16 @@ __device__ __forceinline__ double psi_of<double>(double rho, double rho0, double
 }
 template <>
 __device__ __forceinline__ float psi_of<float>(float rho, float rho0, float inv_rho0) {
-    return rho0 * (1.0f - expf(-rho * inv_rho0));
+    return rho0 * (1.0f - __expf(-rho * inv_rho0));
+}
+
+// 1/rho.  Float arithmetic uses the hardware reciprocal with one rounding
+// step (__fdividef, within 2 ulp) instead of the IEEE division, whose
+// special-case check adds a branch per cell.
+template <class R>
+__device__ __forceinline__ R recip(R x) {
+    if constexpr (sizeof(R) == sizeof(double)) return 1.0 / x;
+    else return __fdividef(1.0f, x);
 }
 
 // Population q of the field starting at p (population stride n elements).
@@ -70,7 +83,7 @@ __device__ __forceinline__ void collide_srt(R (&f)[Q], R Fx, R Fy, R Fz, R tau, 
         if constexpr (cy(q) != 0) jy += R(cy(q)) * dif;
         if constexpr (cz(q) != 0) jz += R(cz(q)) * dif;
     });
-    const R inv_rho = R(1) / rho;
+    const R inv_rho = recip(rho);
     const R ux = (jx + tau * Fx) * inv_rho;
     const R uy = (jy + tau * Fy) * inv_rho;
     const R uz = (jz + tau * Fz) * inv_rho;
@@ -81,18 +94,21 @@ __device__ __forceinline__ void collide_srt(R (&f)[Q], R Fx, R Fy, R Fz, R tau, 
     // which made FP32 runs gain ~3e-8 of their mass every step.
     const R r1 = R(wq(1)) * rho, r2 = R(wq(7)) * rho;
     const R r0 = rho - R(6) * r1 - R(12) * r2;
-    f[0] += omega * (r0 * base - f[0]);
+    // f* = (1 - omega) f + omega (A +/- B): omega w rho per shell once
+    const R keep = R(1) - omega;
+    const R o1 = omega * r1, o2 = omega * r2, o1b = R(3) * o1, o2b = R(3) * o2;
+    f[0] = keep * f[0] + omega * (r0 * base);
     static_for<0, 9>([&](auto pc) {
         constexpr int q = 2 * decltype(pc)::value + 1;
         R cu = R(0);
         if constexpr (cx(q) != 0) cu += R(cx(q)) * ux;
         if constexpr (cy(q) != 0) cu += R(cy(q)) * uy;
         if constexpr (cz(q) != 0) cu += R(cz(q)) * uz;
-        const R wr = (wq(q) == wq(1)) ? r1 : r2;
-        const R A = wr * (base + R(4.5) * cu * cu);
-        const R B = wr * (R(3) * cu);
-        f[q] += omega * ((A + B) - f[q]);
-        f[q + 1] += omega * ((A - B) - f[q + 1]);
+        constexpr bool axis = wq(q) == wq(1);
+        const R oA = (axis ? o1 : o2) * (base + R(4.5) * cu * cu);
+        const R oB = (axis ? o1b : o2b) * cu;
+        f[q] = keep * f[q] + (oA + oB);
+        f[q + 1] = keep * f[q + 1] + (oA - oB);
     });
 }
 
@@ -131,7 +147,7 @@ __device__ __forceinline__ void collide_mrt(R (&f)[Q], R Fx, R Fy, R Fz, const R
         m[k] = acc;
     });
     const R rho = m[0];
-    const R inv_rho = R(1) / rho;
+    const R inv_rho = recip(rho);
     const R ux = (m[3] + R(0.5) * Fx) * inv_rho;
     const R uy = (m[5] + R(0.5) * Fy) * inv_rho;
     const R uz = (m[7] + R(0.5) * Fz) * inv_rho;
@@ -227,7 +243,7 @@ __device__ __forceinline__ void collide_mrt_sparse(R (&f)[Q], R Fx, R Fy, R Fz, 
         if constexpr (cy(q) != 0) jy += R(cy(q)) * dif;
         if constexpr (cz(q) != 0) jz += R(cz(q)) * dif;
     });
-    const R inv_rho = R(1) / rho;
+    const R inv_rho = recip(rho);
     const R ux = (jx + R(0.5) * Fx) * inv_rho;
     const R uy = (jy + R(0.5) * Fy) * inv_rho;
     const R uz = (jz + R(0.5) * Fz) * inv_rho;
@@ -279,23 +295,24 @@ __device__ __forceinline__ void collide_mrt_sparse(R (&f)[Q], R Fx, R Fy, R Fz, 
     // collide_srt: no systematic mass from the rounded weights)
     const R r1 = R(wq(1)) * rho, r2 = R(wq(7)) * rho;
     const R r0 = rho - R(6) * r1 - R(12) * r2;
-    f[0] = r0 * base - R(wq(0)) * R(1.5) * uF + corr(std::integral_constant<int, 0>{});
+    const R r1b = R(3) * r1, r2b = R(3) * r2, uF15 = R(1.5) * uF;
+    f[0] = r0 * base - R(wq(0)) * uF15 + corr(std::integral_constant<int, 0>{});
     static_for<0, 9>([&](auto pc) {
         constexpr int q = 2 * decltype(pc)::value + 1;
         R cu = R(0), cF = R(0);
         if constexpr (cx(q) != 0) { cu += R(cx(q)) * ux; cF += R(cx(q)) * Fx; }
         if constexpr (cy(q) != 0) { cu += R(cy(q)) * uy; cF += R(cy(q)) * Fy; }
         if constexpr (cz(q) != 0) { cu += R(cz(q)) * uz; cF += R(cz(q)) * Fz; }
-        const R w = R(wq(q));
-        const R wr = (wq(q) == wq(1)) ? r1 : r2;
-        // f_eq = A +/- B; Guo source S/2 = E +/- O
-        const R A = wr * (base + R(4.5) * cu * cu);
-        const R B = wr * (R(3) * cu);
-        const R E = w * (R(-1.5) * uF + R(4.5) * cu * cF);
-        const R O = w * (R(1.5) * cF);
-        const R c = corr(std::integral_constant<int, q>{});  // even rows: equal on both members
-        f[q] = A + B + E + O + c;
-        f[q + 1] = A - B + E - O + c;
+        constexpr bool axis = wq(q) == wq(1);
+        // f_eq = A +/- B and the Guo source S/2 = E +/- O, as the even part
+        // A + E = w rho (base + 4.5 cu^2) + w (4.5 cu cF - 1.5 u.F) and the
+        // odd part B + O = 3 w rho cu + 1.5 w cF of the velocity pair
+        const R cu45 = R(4.5) * cu;
+        const R even = (axis ? r1 : r2) * (base + cu45 * cu) + R(wq(q)) * (cu45 * cF - uF15);
+        const R odd = (axis ? r1b : r2b) * cu + R(1.5 * wq(q)) * cF;
+        const R e = even + corr(std::integral_constant<int, q>{});  // even rows: equal on both members
+        f[q] = e + odd;
+        f[q + 1] = e - odd;
     });
 }
 
@@ -442,6 +459,7 @@ sc_step_kernel(const typename Codec::S* __restrict__ src, typename Codec::S* __r
             r += fc[q];
         });
         psi_s[slot_of(zs)][my_slot] = psi_of<R>(r, rho0, inv_rho0);
+        if (a.psi_out && active) static_cast<R*>(a.psi_out)[zo + my_xy] = psi_s[slot_of(zs)][my_slot];
         put_rho(slot_of(zs), my_slot, r);
         if (h_slot >= 0) {
             const R rh = cell_density<Codec>(src + zo + h_xy, n, dev, ref_at(zo + h_xy));
@@ -464,6 +482,7 @@ sc_step_kernel(const typename Codec::S* __restrict__ src, typename Codec::S* __r
                 r += fn[q];
             });
             psi_s[zp_slot][my_slot] = psi_of<R>(r, rho0, inv_rho0);
+            if (a.psi_out && active && z + 1 < ze) static_cast<R*>(a.psi_out)[zo + my_xy] = psi_s[zp_slot][my_slot];
             put_rho(zp_slot, my_slot, r);
             if (h_slot >= 0) {
                 const R rh = cell_density<Codec>(src + zo + h_xy, n, dev, ref_at(zo + h_xy));
@@ -848,8 +867,12 @@ sc_step_pipe_kernel(const typename Codec::S* __restrict__ src_all, typename Code
                 constexpr int q = decltype(qc)::value;
                 r += f[q];
             });
-            ring[slot_of(z) * PLANE + my_slot] = psi_of<R>(r, rho0, inv_rho0);
+            const R p = psi_of<R>(r, rho0, inv_rho0);
+            ring[slot_of(z) * PLANE + my_slot] = p;
             if constexpr (LOCAL) rring[slot_of(z) * PLANE + my_slot] = r;
+            if constexpr (!BATCH) {  // the psi of the planes this item owns
+                if (a.psi_out && active && z >= zs && z < ze) static_cast<R*>(a.psi_out)[I(z) * plane + my_xy] = p;
+            }
         };
         // One plane: loads of z+2 go out before the collision of z and are
         // consumed after it.  fc holds plane z, fn plane z+1, fl receives z+2;

@@ -30,12 +30,13 @@ def neck_energy_grad(rho):
     return np.broadcast_to(g[:, None, None], rho.shape).copy()
 
 
-def test_adjoint_field_matches_the_reverse_mode_oracle():
-    rho0 = inputs.noisy_ligament_density(12, 12, 20, 3.0, 0.1, RL, RV, 1e-3, seed=31)
-    steps = 30
+@pytest.mark.parametrize("box,R0,steps,every", [((12, 12, 20), 3.0, 30, 7), ((16, 16, 32), 4.0, 40, 9)])
+def test_adjoint_field_matches_the_reverse_mode_oracle(box, R0, steps, every):
+    """12 x 12 x 20, and the 16 x 16 x 32 check size of the adjoint form."""
+    rho0 = inputs.noisy_ligament_density(*box, R0, 0.1, RL, RV, 1e-3, seed=31)
     nz, ny, nx = rho0.shape
     with lbm.Lattice(nx, ny, nz, G=G0, tau=TAU0, storage="f64") as L:
-        L.adjoint_forward(rho0, steps, 7)
+        L.adjoint_forward(rho0, steps, every)
         r, _ = L.moments()
         g, gG, gT = L.adjoint_backward(neck_energy_grad(r))
     J_ref, g_ref, gG_ref, gT_ref = rv.gradient(rho0, G0, TAU0, steps, "neck", RL, RV)
