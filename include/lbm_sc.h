@@ -262,6 +262,29 @@ lbm_status lbm_kernel_config(const lbm_ctx *ctx, int *kernel, int *tile_y,
 /* sizeof(lbm_params) in this build, so that bindings can check their layout. */
 long long lbm_params_sizeof(void);
 
+/* Change the step kernel's launch shape: variant, tile height and z planes
+ * per work item (0 = automatic for each), with the same rules as the
+ * lbm_params fields of those names.  Returns LBM_EINVAL (launch shape
+ * unchanged) for a shape that cannot serve this lattice, LBM_ECUDA if it
+ * cannot be configured on this device.  Not for a box of a batch. */
+lbm_status lbm_set_kernel_config(lbm_ctx *ctx, int kernel, int tile_y,
+                                 int zchunk);
+
+/* Autotuner of the step's launch shape: times trial_steps (rounded up to even)
+ * steps of each candidate on this lattice and keeps the fastest.  The
+ * candidates differ in how the psi halo and the populations are staged:
+ * kernel 1 (ring cells loaded into registers), 2 (every population through
+ * cp.async), 3 (register prefetch one plane ahead, ring through cp.async;
+ * with z chunks of 8, 16, 32 planes or automatic), 5 (tensor-copy boxes,
+ * FP32), 7 (paired 16-bit words), each on 32x4, 32x8 and 32x16 tiles
+ * (64-wide for kernel 7); kernel 6 on 32x8 / 32x16 when G2 != 0.  The trial
+ * steps advance whatever state the context holds (its step counter does not
+ * change): tune before setting the initial state.  Outputs (any may be NULL):
+ * the chosen kernel, tile height, z chunk and its time per step in ms.
+ * Returns LBM_ECUDA if no candidate ran. */
+lbm_status lbm_tune(lbm_ctx *ctx, int trial_steps, int *kernel, int *tile_y,
+                    int *zchunk, double *ms_per_step);
+
 /* ---------------------------------------------------------------------------
  * Discrete adjoint of the SRT step (Sec. 2: Eqs. LBE, local_eq, momentum,
  * SC_force, vel_shift), for gradients of an objective J(rho(T)) with respect

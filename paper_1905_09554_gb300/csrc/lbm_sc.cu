@@ -453,6 +453,148 @@ int auto_zchunk(const lbm_ctx* c) {
     return int(zc);
 }
 
+// Why a launch shape (step kernel variant, tile height, z chunk; 0 = auto)
+// cannot serve a lattice with these parameters, or nullptr if it can.  The
+// checks that need a device (occupancy, tensor maps) come later.
+const char* launch_shape_error(const lbm_params& p, int kernel, int tile_y, int zchunk) {
+    if (p.G2 != 0.0 && ((p.storage != LBM_F64 && p.storage != LBM_F32) || (kernel != 0 && kernel != 6) ||
+                        (tile_y != 0 && tile_y != 8 && tile_y != 16)))
+        return "the two-belt force (G2 != 0) runs kernel 6 on 32x8 or 32x16 tiles with FP64/FP32 storage";
+    if (p.G2 == 0.0 && kernel == 6) return "kernel 6 is the two-belt force kernel (needs G2 != 0)";
+    if (p.storage >= LBM_F16_LOCAL && (kernel == 2 || (kernel >= 4 && kernel != 7)))
+        return "local-reference storage runs kernel 1, 3 or 7";
+    if (kernel == 7 && (p.storage < LBM_F16_DEV || p.nx % 2 != 0)) return "kernel 7 needs 16-bit storage and nx even";
+    if (kernel < 0 || kernel > 7) return "kernel must be 0 .. 7";
+    if (tile_y != 0 && tile_y != 4 && tile_y != 8 && tile_y != 16) return "tile_y must be 0, 4, 8 or 16";
+    if (zchunk < 0) return "zchunk must be >= 0";
+    return nullptr;
+}
+
+// Choose and prepare the step kernel of a context: variant `kernel`, tile
+// height `tile_y`, z planes per work item `zchunk` (0 = automatic for each),
+// and derive the persistent grid and work items.  Used by lbm_create and by
+// lbm_set_kernel_config / lbm_tune; on an error the message goes to msg.
+lbm_status configure_step(lbm_ctx* c, int kernel, int tile_y, int zchunk, char* msg, size_t msg_len) {
+    const lbm_params* p = &c->p;
+    const long long n = c->n;
+    StepArgs& a = c->args;
+    c->grid = 0;
+    c->grid3 = 0;
+    // Auto launch shape (measured on GB300 at 256x256x575): FP32 runs the
+    // pipelined kernel, on 32x16 tiles for SRT and unit-rate MRT and on 32x8
+    // tiles for the other MRT kernels (their collision needs more registers
+    // per cell: MRT tau = 0.8 gives 26.4 / 27.8 / 26.9 GLUPS on 32x16 / 32x8 /
+    // 32x4); the 16-bit formats run the pipelined kernel on 32x4 tiles
+    // when nx is even (FP16 SRT 31.9 GLUPS against 30.4 register-staged;
+    // 32x16 tiles 28.9), else the register-staged kernel; FP64 runs the
+    // register-staged kernel on 32x4 tiles.
+    const bool wide_ok = p->storage == LBM_F32 || p->storage == LBM_F64;
+    const bool pipe_default = p->storage == LBM_F32 || (p->storage >= LBM_F16_DEV && p->nx % 2 == 0);
+    // the global-reference 16-bit formats run the paired kernel on 64x8 tiles
+    // (FP16 SRT 35.7 GLUPS against 32.7 for kernel 3 on 32x4 tiles at
+    // 256x256x575); the local-reference ones stay on kernel 3 (30.9 against 29.2)
+    const bool pair_default = (p->storage == LBM_F16_DEV || p->storage == LBM_BF16_DEV) && p->nx % 2 == 0;
+    const int coll = c->coll;
+    const bool wide = wide_ok && (coll == COLL_SRT || coll == COLL_MRT_UNIT) &&
+                      (kernel == 3 || (kernel == 0 && pipe_default));
+    const bool mrt8 = p->storage == LBM_F32 && (coll == COLL_MRT || coll == COLL_MRT_SPARSE) &&
+                      (kernel == 3 || (kernel == 0 && pipe_default));
+    const bool pair = kernel == 7 || (kernel == 0 && pair_default);
+    c->tile_y = tile_y ? tile_y : ((wide || kernel == 5) ? 16 : ((mrt8 || pair) ? 8 : 4));
+    if (p->G2 != 0.0) c->tile_y = tile_y ? tile_y : 8;  // the two-belt kernel
+    if (kernel == 4 && (p->storage != LBM_F32 || p->nx % 4 != 0)) {
+        snprintf(msg, msg_len, "kernel 4 needs FP32 storage and nx %% 4 == 0");
+        return LBM_EINVAL;
+    }
+    if (kernel == 5 && (p->storage != LBM_F32 || c->tile_y < 8 || p->nx % 32 != 0 || p->ny % c->tile_y != 0)) {
+        snprintf(msg, msg_len,
+                 "kernel 5 needs FP32 storage, tile_y 8 or 16, nx %% 32 == 0 and ny %% tile_y == 0");
+        return LBM_EINVAL;
+    }
+    if (kernel < 0 || kernel > 7) {
+        snprintf(msg, msg_len, "kernel must be 0 .. 7");
+        return LBM_EINVAL;
+    }
+    // kernels 3 and 7 address cells with 32-bit offsets within a population
+    const bool off32 = n <= 0xffffffffLL;
+    if (!off32 && (kernel == 3 || kernel == 7)) {
+        snprintf(msg, msg_len, "kernel %d needs nx*ny*nz < 2^32", kernel);
+        return LBM_EINVAL;
+    }
+    c->kernel = p->G2 != 0.0 ? 6 : 1;
+    if (p->G2 == 0.0 && kernel != 1 && !(kernel == 0 && (!pipe_default || !off32))) {
+        c->kernel = kernel == 0 ? (pair_default ? 7 : 3) : kernel;
+        const int per_sm = prepare_async(c);
+        if (per_sm > 0) {
+            c->grid = per_sm * c->num_sms;
+        } else if (kernel >= 2) {
+            if (per_sm < 0)
+                snprintf(msg, msg_len, "kernel %d cannot be configured: %s",
+                         kernel, cudaGetErrorString(cudaError_t(-per_sm)));
+            else
+                snprintf(msg, msg_len,
+                         "kernel %d needs FP64/FP32 storage (kernel 2 with FP64: tile_y <= 8; "
+                         "kernel 3 also takes the 16-bit formats with nx even) and must fit on an SM",
+                         kernel);
+            return LBM_EINVAL;
+        } else {
+            c->kernel = 1;
+        }
+    }
+    if (c->kernel == 5) {
+        c->kernel = 3;
+        const int per3 = prepare_async(c);
+        c->kernel = 5;
+        if (per3 < 1 || encode_tensor_maps(c) != LBM_OK) {
+            snprintf(msg, msg_len, "%s",
+                     c->err[0] ? c->err : "the pipelined kernel cannot be configured");
+            return LBM_ECUDA;
+        }
+        c->grid3 = per3 * c->num_sms;
+    }
+    const int tile_w = c->kernel == 7 ? 64 : 32;  // kernel 7: two cells per thread along x
+    const int tiles_x = (p->nx + tile_w - 1) / tile_w, tiles_y = (p->ny + c->tile_y - 1) / c->tile_y;
+    if (zchunk) {
+        c->zchunk = zchunk < p->nz ? zchunk : p->nz;
+    } else if (c->kernel >= 2 && c->kernel != 6) {
+        // At least about 8 work items per block of the persistent grid, and
+        // short chunks: the address range that all blocks touch at once grows
+        // with the chunk length times the plane size.  Measured on GB300, SRT
+        // on 32x16 tiles (GLUPS for chunks of 16 / 32 / 64 planes):
+        // 256^2 x 575 31.8 / 32.0 / 31.9, 576^2 x 1536 30.1 / 29.8 / 28.4,
+        // 640^2 x 1437 30.3 / 26.6 / 25.2, 672^2 x 1792 28.7 / 22.9 / 21.7;
+        // 512^2 x 1149 with 383-plane chunks 25.8.  So at most 32 planes, and
+        // for 32x16 tiles at most 24 MiB of one population's planes (>= 16);
+        // the 32x4 MRT tiles measured best at 32 on the large boxes.
+        const long long tiles = (long long)tiles_x * tiles_y;
+        long long chunks = (8LL * c->grid + tiles - 1) / tiles;
+        long long zc = (p->nz + chunks - 1) / chunks;
+        long long zmax = 32;
+        if (c->tile_y >= 16) {
+            const long long plane_bytes = (long long)p->nx * p->ny * (long long)c->elem;
+            zmax = (24LL << 20) / (plane_bytes > 0 ? plane_bytes : 1);
+            zmax = zmax < 16 ? 16 : (zmax > 32 ? 32 : zmax);
+            // planes of a population of 1.5 MiB and more (672^2 FP32, the
+            // paper's R0 = 98 box): 8 planes, measured 28.7 GLUPS against
+            // 27.7 / 20.0 / 25.0 for 6 / 12 / 16
+            if (plane_bytes >= (3LL << 19)) zmax = 8;
+        }
+        if (zc > zmax) zc = zmax;
+        if (zc < 8) zc = 8;
+        c->zchunk = int(zc < p->nz ? zc : p->nz);
+    } else {
+        c->zchunk = auto_zchunk(c);
+    }
+    a.zchunk = c->zchunk;
+    a.tiles_x = tiles_x;
+    a.n_tiles = tiles_x * tiles_y;
+    a.n_items = a.n_tiles * ((p->nz + c->zchunk - 1) / c->zchunk);
+    if (c->kernel >= 2 && c->grid > a.n_items) c->grid = a.n_items;
+    if (c->grid3 > a.n_items) c->grid3 = a.n_items;
+
+    return LBM_OK;
+}
+
 }  // namespace
 
 // ----------------------------------------------------------------------------
@@ -508,29 +650,20 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return create_fail(LBM_EINVAL, "lbm_create: tau must be > 0.5");
     if (!std::isfinite(p->G)) return create_fail(LBM_EINVAL, "lbm_create: G must be finite");
     if (!std::isfinite(p->G2)) return create_fail(LBM_EINVAL, "lbm_create: G2 must be finite");
-    if (p->G2 != 0.0 && ((p->storage != LBM_F64 && p->storage != LBM_F32) || (p->kernel != 0 && p->kernel != 6) ||
-                         (p->tile_y != 0 && p->tile_y != 8 && p->tile_y != 16)))
-        return create_fail(LBM_EINVAL, "lbm_create: the two-belt force (G2 != 0) runs kernel 6 on 32x8 or 32x16 "
-                                       "tiles with FP64/FP32 storage");
-    if (p->G2 == 0.0 && p->kernel == 6)
-        return create_fail(LBM_EINVAL, "lbm_create: kernel 6 is the two-belt force kernel (needs G2 != 0)");
+    if (const char* why = launch_shape_error(*p, p->kernel, p->tile_y, p->zchunk)) {
+        snprintf(g_create_err, sizeof(g_create_err), "lbm_create: %s", why);
+        return LBM_EINVAL;
+    }
     if (p->psi != LBM_PSI_EXP) return create_fail(LBM_EINVAL, "lbm_create: unknown psi law");
     if (!(p->rho0 > 0) || !std::isfinite(p->rho0)) return create_fail(LBM_EINVAL, "lbm_create: rho0 must be > 0");
     if (p->storage < LBM_F64 || p->storage > LBM_BF16_LOCAL) return create_fail(LBM_EINVAL, "lbm_create: unknown storage");
     if (p->storage >= LBM_F16_DEV && (!(p->dev_scale > 0) || !std::isfinite(p->rho_ref)))
         return create_fail(LBM_EINVAL, "lbm_create: deviation storage needs dev_scale > 0 and finite rho_ref");
-    if (p->storage >= LBM_F16_LOCAL && (p->kernel == 2 || (p->kernel >= 4 && p->kernel != 7)))
-        return create_fail(LBM_EINVAL, "lbm_create: local-reference storage runs kernel 1, 3 or 7");
-    if (p->kernel == 7 && (p->storage < LBM_F16_DEV || p->nx % 2 != 0))
-        return create_fail(LBM_EINVAL, "lbm_create: kernel 7 needs 16-bit storage and nx even");
     if (p->collision == LBM_MRT_GUO && p->has_rates) {
         for (int k = 0; k < Q; ++k)
             if (!(p->s[k] > 0.0 && p->s[k] < 2.0))
                 return create_fail(LBM_EINVAL, "lbm_create: MRT rates must lie in (0, 2)");
     }
-    if (p->tile_y != 0 && p->tile_y != 4 && p->tile_y != 8 && p->tile_y != 16)
-        return create_fail(LBM_EINVAL, "lbm_create: tile_y must be 0, 4, 8 or 16");
-    if (p->zchunk < 0) return create_fail(LBM_EINVAL, "lbm_create: zchunk must be >= 0");
     if ((p->f_a == nullptr) != (p->f_b == nullptr))
         return create_fail(LBM_EINVAL, "lbm_create: give both f_a and f_b or neither");
     if (p->f_a && ((reinterpret_cast<uintptr_t>(p->f_a) | reinterpret_cast<uintptr_t>(p->f_b)) & 15))
@@ -639,123 +772,14 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     a.dev.rho_ref = float(p->rho_ref);
     a.dev.scale = float(p->dev_scale);
     a.dev.inv_scale = float(1.0 / p->dev_scale);
-    // Auto launch shape (measured on GB300 at 256x256x575): FP32 runs the
-    // pipelined kernel, on 32x16 tiles for SRT and unit-rate MRT and on 32x8
-    // tiles for the other MRT kernels (their collision needs more registers
-    // per cell: MRT tau = 0.8 gives 26.4 / 27.8 / 26.9 GLUPS on 32x16 / 32x8 /
-    // 32x4); the 16-bit formats run the pipelined kernel on 32x4 tiles
-    // when nx is even (FP16 SRT 31.9 GLUPS against 30.4 register-staged;
-    // 32x16 tiles 28.9), else the register-staged kernel; FP64 runs the
-    // register-staged kernel on 32x4 tiles.
-    const bool wide_ok = p->storage == LBM_F32 || p->storage == LBM_F64;
-    const bool pipe_default = p->storage == LBM_F32 || (p->storage >= LBM_F16_DEV && p->nx % 2 == 0);
-    // the global-reference 16-bit formats run the paired kernel on 64x8 tiles
-    // (FP16 SRT 35.7 GLUPS against 32.7 for kernel 3 on 32x4 tiles at
-    // 256x256x575); the local-reference ones stay on kernel 3 (30.9 against 29.2)
-    const bool pair_default = (p->storage == LBM_F16_DEV || p->storage == LBM_BF16_DEV) && p->nx % 2 == 0;
-    const int coll = c->coll;
-    const bool wide = wide_ok && (coll == COLL_SRT || coll == COLL_MRT_UNIT) &&
-                      (p->kernel == 3 || (p->kernel == 0 && pipe_default));
-    const bool mrt8 = p->storage == LBM_F32 && (coll == COLL_MRT || coll == COLL_MRT_SPARSE) &&
-                      (p->kernel == 3 || (p->kernel == 0 && pipe_default));
-    const bool pair = p->kernel == 7 || (p->kernel == 0 && pair_default);
-    c->tile_y = p->tile_y ? p->tile_y : ((wide || p->kernel == 5) ? 16 : ((mrt8 || pair) ? 8 : 4));
-    if (p->G2 != 0.0) c->tile_y = p->tile_y ? p->tile_y : 8;  // the two-belt kernel
-    if (p->kernel == 4 && (p->storage != LBM_F32 || p->nx % 4 != 0)) {
-        snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel 4 needs FP32 storage and nx %% 4 == 0");
-        lbm_destroy(c);
-        return LBM_EINVAL;
-    }
-    if (p->kernel == 5 && (p->storage != LBM_F32 || c->tile_y < 8 || p->nx % 32 != 0 || p->ny % c->tile_y != 0)) {
-        snprintf(g_create_err, sizeof(g_create_err),
-                 "lbm_create: kernel 5 needs FP32 storage, tile_y 8 or 16, nx %% 32 == 0 and ny %% tile_y == 0");
-        lbm_destroy(c);
-        return LBM_EINVAL;
-    }
-    if (p->kernel < 0 || p->kernel > 7) {
-        snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel must be 0 .. 7");
-        lbm_destroy(c);
-        return LBM_EINVAL;
-    }
-    // kernels 3 and 7 address cells with 32-bit offsets within a population
-    const bool off32 = n <= 0xffffffffLL;
-    if (!off32 && (p->kernel == 3 || p->kernel == 7)) {
-        snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel %d needs nx*ny*nz < 2^32", p->kernel);
-        lbm_destroy(c);
-        return LBM_EINVAL;
-    }
-    c->kernel = p->G2 != 0.0 ? 6 : 1;
-    if (p->G2 == 0.0 && p->kernel != 1 && !(p->kernel == 0 && (!pipe_default || !off32))) {
-        c->kernel = p->kernel == 0 ? (pair_default ? 7 : 3) : p->kernel;
-        const int per_sm = prepare_async(c);
-        if (per_sm > 0) {
-            c->grid = per_sm * c->num_sms;
-        } else if (p->kernel >= 2) {
-            if (per_sm < 0)
-                snprintf(g_create_err, sizeof(g_create_err), "lbm_create: kernel %d cannot be configured: %s",
-                         p->kernel, cudaGetErrorString(cudaError_t(-per_sm)));
-            else
-                snprintf(g_create_err, sizeof(g_create_err),
-                         "lbm_create: kernel %d needs FP64/FP32 storage (kernel 2 with FP64: tile_y <= 8; "
-                         "kernel 3 also takes the 16-bit formats with nx even) and must fit on an SM",
-                         p->kernel);
+    {
+        char why[400] = {0};
+        if (lbm_status st = configure_step(c, p->kernel, p->tile_y, p->zchunk, why, sizeof(why)); st != LBM_OK) {
+            snprintf(g_create_err, sizeof(g_create_err), "lbm_create: %s", why);
             lbm_destroy(c);
-            return LBM_EINVAL;
-        } else {
-            c->kernel = 1;
+            return st;
         }
     }
-    if (c->kernel == 5) {
-        c->kernel = 3;
-        const int per3 = prepare_async(c);
-        c->kernel = 5;
-        if (per3 < 1 || encode_tensor_maps(c) != LBM_OK) {
-            snprintf(g_create_err, sizeof(g_create_err), "lbm_create: %s",
-                     c->err[0] ? c->err : "the pipelined kernel cannot be configured");
-            lbm_destroy(c);
-            return LBM_ECUDA;
-        }
-        c->grid3 = per3 * c->num_sms;
-    }
-    const int tile_w = c->kernel == 7 ? 64 : 32;  // kernel 7: two cells per thread along x
-    const int tiles_x = (p->nx + tile_w - 1) / tile_w, tiles_y = (p->ny + c->tile_y - 1) / c->tile_y;
-    if (p->zchunk) {
-        c->zchunk = p->zchunk < p->nz ? p->zchunk : p->nz;
-    } else if (c->kernel >= 2 && c->kernel != 6) {
-        // At least about 8 work items per block of the persistent grid, and
-        // short chunks: the address range that all blocks touch at once grows
-        // with the chunk length times the plane size.  Measured on GB300, SRT
-        // on 32x16 tiles (GLUPS for chunks of 16 / 32 / 64 planes):
-        // 256^2 x 575 31.8 / 32.0 / 31.9, 576^2 x 1536 30.1 / 29.8 / 28.4,
-        // 640^2 x 1437 30.3 / 26.6 / 25.2, 672^2 x 1792 28.7 / 22.9 / 21.7;
-        // 512^2 x 1149 with 383-plane chunks 25.8.  So at most 32 planes, and
-        // for 32x16 tiles at most 24 MiB of one population's planes (>= 16);
-        // the 32x4 MRT tiles measured best at 32 on the large boxes.
-        const long long tiles = (long long)tiles_x * tiles_y;
-        long long chunks = (8LL * c->grid + tiles - 1) / tiles;
-        long long zc = (p->nz + chunks - 1) / chunks;
-        long long zmax = 32;
-        if (c->tile_y >= 16) {
-            const long long plane_bytes = (long long)p->nx * p->ny * (long long)c->elem;
-            zmax = (24LL << 20) / (plane_bytes > 0 ? plane_bytes : 1);
-            zmax = zmax < 16 ? 16 : (zmax > 32 ? 32 : zmax);
-            // planes of a population of 1.5 MiB and more (672^2 FP32, the
-            // paper's R0 = 98 box): 8 planes, measured 28.7 GLUPS against
-            // 27.7 / 20.0 / 25.0 for 6 / 12 / 16
-            if (plane_bytes >= (3LL << 19)) zmax = 8;
-        }
-        if (zc > zmax) zc = zmax;
-        if (zc < 8) zc = 8;
-        c->zchunk = int(zc < p->nz ? zc : p->nz);
-    } else {
-        c->zchunk = auto_zchunk(c);
-    }
-    a.zchunk = c->zchunk;
-    a.tiles_x = tiles_x;
-    a.n_tiles = tiles_x * tiles_y;
-    a.n_items = a.n_tiles * ((p->nz + c->zchunk - 1) / c->zchunk);
-    if (c->kernel >= 2 && c->grid > a.n_items) c->grid = a.n_items;
-    if (c->grid3 > a.n_items) c->grid3 = a.n_items;
 
     e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -825,6 +849,91 @@ lbm_status lbm_kernel_config(const lbm_ctx* c, int* kernel, int* tile_y, int* zc
 }
 
 long long lbm_params_sizeof(void) { return (long long)sizeof(lbm_params); }
+
+lbm_status lbm_set_kernel_config(lbm_ctx* c, int kernel, int tile_y, int zchunk) {
+    if (!c) return LBM_EINVAL;
+    if (c->batch) return c->fail(LBM_EINVAL, "lbm_set_kernel_config: this context is a box of a batch");
+    if (const char* why = launch_shape_error(c->p, kernel, tile_y, zchunk))
+        return c->fail(LBM_EINVAL, "lbm_set_kernel_config: %s", why);
+    const int k0 = c->kernel, t0 = c->tile_y, z0 = c->zchunk;
+    char why[400] = {0};
+    const lbm_status st = configure_step(c, kernel, tile_y, zchunk, why, sizeof(why));
+    if (st != LBM_OK) {
+        char ignored[400];
+        configure_step(c, k0, t0, z0, ignored, sizeof(ignored));  // the previous shape worked
+        return c->fail(st, "lbm_set_kernel_config: %s", why);
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_tune(lbm_ctx* c, int trial_steps, int* kernel, int* tile_y, int* zchunk, double* ms_per_step) {
+    if (!c) return LBM_EINVAL;
+    if (c->batch) return c->fail(LBM_EINVAL, "lbm_tune: this context is a box of a batch (use lbm_batch_tune)");
+    if (trial_steps < 1) return c->fail(LBM_EINVAL, "lbm_tune: trial_steps must be >= 1");
+    struct Shape {
+        int kernel, tile_y, zchunk;
+    };
+    std::vector<Shape> shapes;
+    const lbm_params& p = c->p;
+    const bool b16 = p.storage >= LBM_F16_DEV, even = p.nx % 2 == 0;
+    for (int ty : {4, 8, 16}) {
+        if (p.G2 != 0.0) {
+            if (ty >= 8) shapes.push_back({6, ty, 0});
+            continue;
+        }
+        shapes.push_back({1, ty, 0});                                          // register-staged ring
+        if (!b16) shapes.push_back({2, ty, 0});                                // every population through cp.async
+        if (!b16 || even)
+            for (int zc : {0, 8, 16, 32}) shapes.push_back({3, ty, zc});       // register prefetch, cp.async ring
+        if (p.storage == LBM_F32 && ty >= 8) shapes.push_back({5, ty, 0});     // tensor-copy boxes
+        if (b16 && even)
+            for (int zc : {0, 16}) shapes.push_back({7, ty, zc});              // paired words
+    }
+    const int k0 = c->kernel, t0 = c->tile_y, z0 = c->zchunk;
+    cudaEvent_t e0, e1;
+    LBM_CUDA(c, cudaEventCreate(&e0));
+    LBM_CUDA(c, cudaEventCreate(&e1));
+    float best = -1.0f;
+    Shape pick{k0, t0, z0};
+    const int steps = trial_steps + (trial_steps & 1);  // even: the state ends in the current copy
+    for (const Shape& sh : shapes) {
+        if (launch_shape_error(p, sh.kernel, sh.tile_y, sh.zchunk)) continue;
+        char why[400];
+        if (configure_step(c, sh.kernel, sh.tile_y, sh.zchunk, why, sizeof(why)) != LBM_OK) continue;
+        const int cur = c->cur;
+        bool ok = launch_step(c, c->f[cur], c->f[cur ^ 1]) == cudaSuccess &&
+                  launch_step(c, c->f[cur ^ 1], c->f[cur]) == cudaSuccess;  // warm-up
+        if (!ok) continue;
+        cudaEventRecord(e0, c->stream);
+        for (int k = 0; k < steps && ok; ++k)
+            ok = launch_step(c, c->f[cur ^ (k & 1)], c->f[cur ^ (~k & 1)]) == cudaSuccess;
+        cudaEventRecord(e1, c->stream);
+        if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= steps;
+        if (best < 0.0f || ms < best) {
+            best = ms;
+            pick = sh;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();  // a shape that failed to launch is skipped, not an error
+    char why[400] = {0};
+    lbm_status st = configure_step(c, pick.kernel, pick.tile_y, pick.zchunk, why, sizeof(why));
+    if (st != LBM_OK) {
+        char ignored[400];
+        configure_step(c, k0, t0, z0, ignored, sizeof(ignored));
+        return c->fail(st, "lbm_tune: %s", why);
+    }
+    if (best < 0.0f) return c->fail(LBM_ECUDA, "lbm_tune: no launch shape ran");
+    if (kernel) *kernel = c->kernel;
+    if (tile_y) *tile_y = c->tile_y;
+    if (zchunk) *zchunk = c->zchunk;
+    if (ms_per_step) *ms_per_step = best;
+    return LBM_OK;
+}
 
 lbm_status lbm_init_ligament(lbm_ctx* c, double R0, double eps, int n_waves, double width, double rho_l,
                              double rho_v) {

@@ -88,6 +88,9 @@ _SIGNATURES = {
     "lbm_params_sizeof": (ctypes.c_longlong, []),
     "lbm_kernel_config": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "lbm_set_kernel_config": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "lbm_tune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_int), _D]),
     "lbm_batch_create": (ctypes.c_int, [ctypes.POINTER(lbm_params), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(_P)]),
     "lbm_batch_destroy": (None, [_P]),
@@ -301,6 +304,17 @@ def lbm_kernel_config(ctx):
 
 
 # ------------------------------------------------------------ object wrapper
+def lbm_set_kernel_config(ctx, kernel, tile_y, zchunk):
+    return load().lbm_set_kernel_config(ctx, int(kernel), int(tile_y), int(zchunk))
+
+
+def lbm_tune(ctx, trial_steps):
+    k, t, z = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    ms = ctypes.c_double()
+    st = load().lbm_tune(ctx, int(trial_steps), ctypes.byref(k), ctypes.byref(t), ctypes.byref(z), ctypes.byref(ms))
+    return st, {"kernel": k.value, "tile_y": t.value, "zchunk": z.value, "ms_per_step": ms.value}
+
+
 def _host_ptr(a: np.ndarray):
     return a.ctypes.data_as(_P)
 
@@ -534,6 +548,34 @@ class Lattice:
         st, cfg = lbm_kernel_config(self.ctx)
         self._check(st)
         return cfg
+
+    def set_kernel_config(self, kernel=0, tile_y=0, zchunk=0):
+        self._check(lbm_set_kernel_config(self.ctx, kernel, tile_y, zchunk))
+
+    def tune(self, trial_steps=3, cache=None):
+        """Pick the step's launch shape (kernel variant, tile height, z chunk)
+        by timing the candidates on this lattice (lbm_tune); tune before
+        setting the initial state, since the trial steps advance it.  With
+        `cache` (a JSON file path) a pick stored for the same box, parameters
+        and GPU model is applied without timing, and a new pick is stored.
+        Returns the pick (kernel, tile_y, zchunk, ms_per_step, cached)."""
+        key = None
+        if cache is not None:
+            p = self.params
+            phys = {"storage": self.storage, "collision": int(p.collision), "G": p.G, "G2": p.G2, "tau": p.tau,
+                    "rates": [p.s[k] for k in range(19)] if p.has_rates else None}
+            key = "lattice:" + _tune_key([self.shape[::-1]], phys)
+            hit = _read_tune_cache(cache).get(key)
+            if hit:
+                self.set_kernel_config(hit["kernel"], hit["tile_y"], hit["zchunk"])
+                return dict(hit, cached=True)
+        st, pick = lbm_tune(self.ctx, trial_steps)
+        self._check(st)
+        if key is not None:
+            data = _read_tune_cache(cache)
+            data[key] = pick
+            _write_tune_cache(cache, data)
+        return dict(pick, cached=False)
 
 
 class _BoxView(Lattice):
