@@ -253,6 +253,46 @@ def test_batch_tune_cache(monkeypatch, tmp_path):
     assert calls["tune"] == 2 and calls["create"][-1] == (8, 32)
 
 
+def test_lattice_tune_cache(monkeypatch, tmp_path):
+    """Lattice.tune(cache=...) tunes once per box / parameters / GPU and
+    stores the pick; a lattice with the same key applies the stored shape
+    through lbm_set_kernel_config without tuning.  (Stand-ins for the
+    library calls: no device work.)"""
+    calls = {"tune": 0, "set": []}
+
+    def fake_tune(ctx, trial_steps):
+        calls["tune"] += 1
+        return lbm.LBM_OK, {"kernel": 3, "tile_y": 16, "zchunk": 24, "ms_per_step": 1.25}
+
+    def fake_set(ctx, kernel, tile_y, zchunk):
+        calls["set"].append((kernel, tile_y, zchunk))
+        return lbm.LBM_OK
+
+    monkeypatch.setattr(lbm, "lbm_tune", fake_tune)
+    monkeypatch.setattr(lbm, "lbm_set_kernel_config", fake_set)
+
+    class Stand(lbm.Lattice):
+        def __init__(self, nx, ny, nz, **kw):  # no context: only what tune() reads
+            self.params = lbm._params(**kw)
+            self.shape = (nz, ny, nx)
+            self.storage = kw.get("storage", "f32")
+            self.ctx = None
+
+        def close(self):
+            pass
+
+    cache = str(tmp_path / "tune.json")
+    first = Stand(64, 32, 24, tau=1.0).tune(cache=cache)
+    assert not first["cached"] and calls["tune"] == 1 and calls["set"] == []
+    again = Stand(64, 32, 24, tau=1.0).tune(cache=cache)
+    assert again["cached"] and calls["tune"] == 1 and calls["set"] == [(3, 16, 24)]
+    Stand(64, 32, 24, tau=0.8).tune(cache=cache)  # other physics: own entry
+    Stand(64, 32, 25, tau=1.0).tune(cache=cache)  # other box: own entry
+    assert calls["tune"] == 3
+    import json
+    assert len(json.load(open(cache))) == 3
+
+
 def _fnv1a64_words(data: bytes) -> int:
     """64-bit FNV-1a over little-endian 64-bit words, the byte tail one byte
     at a time (the checkpoint checksum's stated definition)."""
