@@ -366,6 +366,7 @@ def measure_forms(device, clocks):
                         "f64_adjoint_steps_per_s": adj["T"] / d["bwd_s"],
                         "f32_forward_with_checkpoints_steps_per_s": adj["T"] / a["fwd_s"],
                         "f32_vs_f64_gradient": adj["fp32_vs_fp64"],
+                        "step_launch_shape": {"f32": adj["f32_tune"], "f64": adj["f64_tune"]},
                         "workload": "64x64x180 ligament, neck energy at step 500, checkpoints every 23"}
     return forms
 
@@ -719,6 +720,8 @@ def measure_adjoint(T=500, every=23):
     out = {}
     for storage in ("f32", "f64"):
         with lbm.Lattice(nx, ny, nz, G=-5.5, tau=1.0, storage=storage) as L:
+            # the recomputation steps this small box many times: pick its launch shape
+            out[storage + "_tune"] = L.tune(trial_steps=4)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             L.adjoint_forward(rho0, T, every)
@@ -756,6 +759,7 @@ def run_adjoint(args):
                                "G=-5.5, SRT tau=1, objective: neck energy at step 500",
                    "checkpoint_every": out["every"], "cells": out["cells"]},
         "forward_with_checkpoints_steps_per_s": T / a["fwd_s"],
+        "step_launch_shape": {"f32": out["f32_tune"], "f64": out["f64_tune"]},
         "fp64": {"adjoint_steps_per_s": T / b["bwd_s"], "dJ_dG": b["dG"], "dJ_dtau": b["dtau"], "J": b["J"]},
         "fp32": {"dJ_dG": a["dG"], "dJ_dtau": a["dtau"], "J": a["J"]},
         "fp32_vs_fp64": out["fp32_vs_fp64"],

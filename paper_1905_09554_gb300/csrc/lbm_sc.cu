@@ -480,27 +480,20 @@ lbm_status configure_step(lbm_ctx* c, int kernel, int tile_y, int zchunk, char* 
     StepArgs& a = c->args;
     c->grid = 0;
     c->grid3 = 0;
-    // Auto launch shape (measured on GB300 at 256x256x575): FP32 runs the
-    // pipelined kernel, on 32x16 tiles for SRT and unit-rate MRT and on 32x8
-    // tiles for the other MRT kernels (their collision needs more registers
-    // per cell: MRT tau = 0.8 gives 26.4 / 27.8 / 26.9 GLUPS on 32x16 / 32x8 /
-    // 32x4); the 16-bit formats run the pipelined kernel on 32x4 tiles
-    // when nx is even (FP16 SRT 31.9 GLUPS against 30.4 register-staged;
-    // 32x16 tiles 28.9), else the register-staged kernel; FP64 runs the
-    // register-staged kernel on 32x4 tiles.
-    const bool wide_ok = p->storage == LBM_F32 || p->storage == LBM_F64;
+    // Auto launch shape (measured on GB300 at 256x256x575, GLUPS): FP32 runs
+    // the pipelined kernel on 32x16 tiles (SRT 32.4; MRT tau = 0.8 30.2
+    // against 28.8 on 32x8 and 26.9 on 32x4); the global-reference 16-bit
+    // formats run the paired kernel on 64x8 tiles (FP16 SRT 35.6 against 32.7
+    // for kernel 3 on 32x4), the local-reference ones kernel 3 on 32x8 tiles
+    // (33.2 against 31.1 on 32x4, 29.8 on 32x16, 29.2 paired, 22.9
+    // register-staged); 16-bit storage with nx odd and FP64 run the
+    // register-staged kernel on 32x4 tiles (FP64 is bound by its FP64 pipe).
     const bool pipe_default = p->storage == LBM_F32 || (p->storage >= LBM_F16_DEV && p->nx % 2 == 0);
-    // the global-reference 16-bit formats run the paired kernel on 64x8 tiles
-    // (FP16 SRT 35.7 GLUPS against 32.7 for kernel 3 on 32x4 tiles at
-    // 256x256x575); the local-reference ones stay on kernel 3 (30.9 against 29.2)
     const bool pair_default = (p->storage == LBM_F16_DEV || p->storage == LBM_BF16_DEV) && p->nx % 2 == 0;
-    const int coll = c->coll;
-    const bool wide = wide_ok && (coll == COLL_SRT || coll == COLL_MRT_UNIT) &&
-                      (kernel == 3 || (kernel == 0 && pipe_default));
-    const bool mrt8 = p->storage == LBM_F32 && (coll == COLL_MRT || coll == COLL_MRT_SPARSE) &&
-                      (kernel == 3 || (kernel == 0 && pipe_default));
+    const bool pipe = kernel == 3 || (kernel == 0 && pipe_default && !pair_default);
     const bool pair = kernel == 7 || (kernel == 0 && pair_default);
-    c->tile_y = tile_y ? tile_y : ((wide || kernel == 5) ? 16 : ((mrt8 || pair) ? 8 : 4));
+    const int auto_ty = (kernel == 5 || (pipe && p->storage <= LBM_F32)) ? 16 : ((pipe || pair) ? 8 : 4);
+    c->tile_y = tile_y ? tile_y : auto_ty;
     if (p->G2 != 0.0) c->tile_y = tile_y ? tile_y : 8;  // the two-belt kernel
     if (kernel == 4 && (p->storage != LBM_F32 || p->nx % 4 != 0)) {
         snprintf(msg, msg_len, "kernel 4 needs FP32 storage and nx %% 4 == 0");
