@@ -534,14 +534,14 @@ def run_ours(args):
         achieved = fpc * ncell / (kernel_ms / 1e3) / 1e12
         peak_alu, peak_src = fp64_peak(local, clocks)
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
-                    "frac": achieved / peak_alu, "traffic": load_traffic(args, ncell, L_info),
+                    "frac": achieved / peak_alu, "traffic": load_traffic(args, ncell, L_info, (nx, ny, nz)),
                     "peak_source": peak_src,
                     "kernel": kname, "fp64_flops_per_cell": fpc, "kernel_ms": kernel_ms,
                     "hbm_frac": bpc * ncell / (kernel_ms / 1e3) / 1e9 / peak}
     else:
         achieved = bpc * ncell / (kernel_ms / 1e3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": load_traffic(args, ncell, L_info),
+                    "frac": achieved / peak, "traffic": load_traffic(args, ncell, L_info, (nx, ny, nz)),
                     "peak_source": f"{src} HBM copy bandwidth",
                     "kernel": kname, "algorithmic_bytes_per_cell": bpc, "kernel_ms": kernel_ms}
 
@@ -597,6 +597,9 @@ def fp64_peak(device, clocks=None):
     return peak, f"FP64 pipe: {sms} SMs x 2 lanes/clk x {mhz:.0f} MHz ({src}) x 2 flop (derived)"
 
 
+STEP_SOURCES = ("step_kernel.cuh", "codec.cuh", "lattice.cuh", "step_multirange.cuh", "e8.cuh", "step_pair16.cuh")
+
+
 def step_record():
     """The committed ncu record for the current step-kernel source, or None
     once the kernel has changed since the counters were taken."""
@@ -607,20 +610,26 @@ def step_record():
     with open(path) as fh:
         rec = json.load(fh)
     h = hashlib.sha256()
-    for f in ("step_kernel.cuh", "codec.cuh", "lattice.cuh", "step_multirange.cuh", "e8.cuh"):
+    for f in STEP_SOURCES:
         with open(os.path.join(ROOT, "paper_1905_09554_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return rec if rec.get("kernel_sha256") == h.hexdigest() else None
 
 
-def load_traffic(args, ncell, info):
+def traffic_key(dims, args, info):
+    nx, ny, nz = dims
+    return (f"{nx}x{ny}x{nz}_{args.collision}_{args.storage}_tau{args.tau:g}_k{info['kernel']}"
+            f"_ty{info['tile_y']}_zc{info['zchunk']}")
+
+
+def load_traffic(args, ncell, info, dims=None):
     """DRAM bytes per launch from the committed ncu record, if it was taken on
-    the current kernel source and this collision/storage/tau/launch shape
-    (kernel variant, tile height, z-chunk length)."""
+    the current kernel source, this box and this collision/storage/tau/launch
+    shape (kernel variant, tile height, z-chunk length)."""
     rec = step_record()
-    if rec is None:
+    if rec is None or dims is None:
         return None
-    key = f"{args.collision}_{args.storage}_tau{args.tau:g}_k{info['kernel']}_ty{info['tile_y']}_zc{info['zchunk']}"
+    key = traffic_key(dims, args, info)
     per = rec.get("bytes_per_cell", {}).get(key)
     return per * ncell if per is not None else None
 

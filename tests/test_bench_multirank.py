@@ -68,10 +68,12 @@ def test_traffic_record_lookup_by_kernel_source_and_launch_shape():
     args = argparse.Namespace(collision="srt", storage="f32", tau=1.0)
     info = {"kernel": 3, "tile_y": 16, "zchunk": 32}
     n = 37_683_200
-    per_cell = rec["bytes_per_cell"]["srt_f32_tau1_k3_ty16_zc32"]
+    dims = (256, 256, 575)
+    per_cell = rec["bytes_per_cell"]["256x256x575_srt_f32_tau1_k3_ty16_zc32"]
     assert 152.0 <= per_cell < 160.0
-    assert bench.load_traffic(args, n, info) == pytest.approx(per_cell * n)
-    assert bench.load_traffic(args, n, dict(info, zchunk=58)) is None
+    assert bench.load_traffic(args, n, info, dims) == pytest.approx(per_cell * n)
+    assert bench.load_traffic(args, n, dict(info, zchunk=58), dims) is None
+    assert bench.load_traffic(args, n, info, (256, 256, 576)) is None
 
 
 def test_reference_arm_prints_the_contract_line_and_other_ranks_stay_silent():
