@@ -126,7 +126,7 @@ template <class Codec, int COLL, int TY>
 cudaError_t launch_batch_t(const StepLaunch& c, const BatchArgs& b, const void* src, void* dst) {
     constexpr int TX = 32;
     const size_t sm = PipeLayout<Codec, TX, TY>::bytes;
-    sc_step_pipe_kernel<Codec, COLL, TX, TY, long long, true><<<c.grid, TX * TY, sm, c.stream>>>(
+    sc_step_pipe_kernel<Codec, COLL, TX, TY, unsigned, true><<<c.grid, TX * TY, sm, c.stream>>>(
         static_cast<const typename Codec::S*>(src), static_cast<typename Codec::S*>(dst), c.args, b);
     return cudaGetLastError();
 }
@@ -135,7 +135,7 @@ template <class Codec, int COLL, int TY>
 int prepare_batch_t(const StepLaunch&) {
     constexpr int TX = 32;
     using Lay = PipeLayout<Codec, TX, TY>;
-    auto kern = sc_step_pipe_kernel<Codec, COLL, TX, TY, long long, true>;
+    auto kern = sc_step_pipe_kernel<Codec, COLL, TX, TY, unsigned, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes);
     int per_sm = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, Lay::bytes);
