@@ -68,8 +68,8 @@ def _save_progress(L, path, state):
     with open(tmp, "w") as fh:
         json.dump(dict(state, lattice=os.path.basename(lat)), fh)
     os.replace(tmp, path + ".json")
-    for old in glob.glob(glob.escape(path) + ".t*"):
-        if old != lat and not old.endswith(".tmp"):
+    for old in glob.glob(glob.escape(path) + ".t[0-9]*"):
+        if old != lat and old[len(path) + 2:].isdigit():
             os.remove(old)
 
 
