@@ -4,8 +4,9 @@
 //  F64: double storage, double arithmetic.
 //  F32: float storage, float arithmetic.
 //  F16Dev / BF16Dev: 16-bit storage of the deviation from the rest
-//     equilibrium at the reference density, d_a = (f_a - w_a rho_ref) * scale,
-//     decoded to float; arithmetic in float.
+//     equilibrium at the reference density, d_a = (f_a - w_a rho_ref) * scale
+//     with w_a rho_ref rounded to float once (DevParams::wrho), decoded to
+//     float; arithmetic in float.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -20,7 +21,19 @@ struct DevParams {
     float rho_ref;
     float scale;
     float inv_scale;
+    float wrho[Q];  // w_a rho_ref in float: the rest equilibrium the deviations are taken from
 };
+
+// The parameters of the deviation formats for a reference density and scale
+// (filled the same way on the host and the device).
+__host__ __device__ inline DevParams make_dev_params(double rho_ref, double scale) {
+    DevParams d;
+    d.rho_ref = float(rho_ref);
+    d.scale = float(scale);
+    d.inv_scale = float(1.0 / scale);
+    for (int q = 0; q < Q; ++q) d.wrho[q] = float(wq(q)) * d.rho_ref;
+    return d;
+}
 
 struct CodecF64 {
     static constexpr bool kLocal = false;
@@ -48,43 +61,50 @@ struct CodecF32 {
     __device__ __forceinline__ static void store(S* p, R v, const DevParams&) { *p = v; }
 };
 
-struct CodecF16Dev {
-    static constexpr bool kLocal = false;
-    using S = __half;
-    using R = float;
-    static constexpr int kStorage = 2;
-    template <int q>
-    __device__ __forceinline__ static R decode(S v, const DevParams& d) {
-        return float(wq(q)) * d.rho_ref + __half2float(v) * d.inv_scale;
+// Conversions of one 16-bit type.
+template <class S16>
+struct Half16 {
+    __device__ __forceinline__ static float to_f(S16 v) {
+        if constexpr (std::is_same<S16, __half>::value) return __half2float(v);
+        else return __bfloat162float(v);
     }
-    template <int q>
-    __device__ __forceinline__ static R load(const S* p, const DevParams& d) { return decode<q>(__ldg(p), d); }
-    template <int q>
-    __device__ __forceinline__ static S encode(R v, const DevParams& d) {
-        return __float2half_rn((v - float(wq(q)) * d.rho_ref) * d.scale);
+    __device__ __forceinline__ static S16 from_f(float v) {
+        if constexpr (std::is_same<S16, __half>::value) return __float2half_rn(v);
+        else return __float2bfloat16_rn(v);
     }
-    template <int q>
-    __device__ __forceinline__ static void store(S* p, R v, const DevParams& d) { *p = encode<q>(v, d); }
 };
 
-struct CodecBF16Dev {
+// Deviations from the rest equilibrium at one global reference density:
+// f_a = w_a rho_ref + d_a / scale, d_a rounded to S16.
+template <class S16, int STORAGE>
+struct CodecDev16 {
     static constexpr bool kLocal = false;
-    using S = __nv_bfloat16;
+    using S = S16;
     using R = float;
-    static constexpr int kStorage = 3;
+    static constexpr int kStorage = STORAGE;
+    __device__ __forceinline__ static float to_f(S v) { return Half16<S16>::to_f(v); }
+    __device__ __forceinline__ static S from_f(float v) { return Half16<S16>::from_f(v); }
+    // population from the stored deviation already widened to float
     template <int q>
-    __device__ __forceinline__ static R decode(S v, const DevParams& d) {
-        return float(wq(q)) * d.rho_ref + __bfloat162float(v) * d.inv_scale;
+    __device__ __forceinline__ static R decode_f(float h, const DevParams& d) {
+        return fmaf(h, d.inv_scale, d.wrho[q]);
     }
+    template <int q>
+    __device__ __forceinline__ static R decode(S v, const DevParams& d) { return decode_f<q>(to_f(v), d); }
     template <int q>
     __device__ __forceinline__ static R load(const S* p, const DevParams& d) { return decode<q>(__ldg(p), d); }
+    // the deviation before its rounding to S
     template <int q>
-    __device__ __forceinline__ static S encode(R v, const DevParams& d) {
-        return __float2bfloat16_rn((v - float(wq(q)) * d.rho_ref) * d.scale);
+    __device__ __forceinline__ static float deviation(R v, const DevParams& d) {
+        return (v - d.wrho[q]) * d.scale;
     }
+    template <int q>
+    __device__ __forceinline__ static S encode(R v, const DevParams& d) { return from_f(deviation<q>(v, d)); }
     template <int q>
     __device__ __forceinline__ static void store(S* p, R v, const DevParams& d) { *p = encode<q>(v, d); }
 };
+using CodecF16Dev = CodecDev16<__half, 2>;
+using CodecBF16Dev = CodecDev16<__nv_bfloat16, 3>;
 
 
 // Local-reference 16-bit storage: each cell also keeps, in a float field,
@@ -99,14 +119,8 @@ struct CodecLocal16 {
     using S = S16;
     using R = float;
     static constexpr int kStorage = std::is_same<S16, __half>::value ? 4 : 5;
-    __device__ __forceinline__ static float to_f(S v) {
-        if constexpr (std::is_same<S16, __half>::value) return __half2float(v);
-        else return __bfloat162float(v);
-    }
-    __device__ __forceinline__ static S from_f(float v) {
-        if constexpr (std::is_same<S16, __half>::value) return __float2half_rn(v);
-        else return __float2bfloat16_rn(v);
-    }
+    __device__ __forceinline__ static float to_f(S v) { return Half16<S16>::to_f(v); }
+    __device__ __forceinline__ static S from_f(float v) { return Half16<S16>::from_f(v); }
     template <int q>
     __device__ __forceinline__ static R decode_ref(S v, float ref, const DevParams& d) {
         return float(wq(q)) * ref + to_f(v) * d.inv_scale;
@@ -115,9 +129,14 @@ struct CodecLocal16 {
     __device__ __forceinline__ static R load_ref(const S* p, float ref, const DevParams& d) {
         return decode_ref<q>(__ldg(p), ref, d);
     }
+    // the deviation before its rounding to S
+    template <int q>
+    __device__ __forceinline__ static float deviation_ref(R v, float ref, const DevParams& d) {
+        return (v - float(wq(q)) * ref) * d.scale;
+    }
     template <int q>
     __device__ __forceinline__ static S encode_ref(R v, float ref, const DevParams& d) {
-        return from_f((v - float(wq(q)) * ref) * d.scale);
+        return from_f(deviation_ref<q>(v, ref, d));
     }
     template <int q>
     __device__ __forceinline__ static void store_ref(S* p, R v, float ref, const DevParams& d) {
@@ -140,13 +159,14 @@ template <>
 __device__ __forceinline__ double decode_rt<CodecF64>(const double* p, float, const DevParams&) { return *p; }
 template <>
 __device__ __forceinline__ double decode_rt<CodecF32>(const float* p, float, const DevParams&) { return *p; }
+// (w_a rho_ref rounded to float first, as in DevParams::wrho)
 template <>
 __device__ __forceinline__ double decode_rt<CodecF16Dev>(const __half* p, float w, const DevParams& d) {
-    return double(w * d.rho_ref + __half2float(*p) * d.inv_scale);
+    return double(fmaf(__half2float(*p), d.inv_scale, __fmul_rn(w, d.rho_ref)));
 }
 template <>
 __device__ __forceinline__ double decode_rt<CodecBF16Dev>(const __nv_bfloat16* p, float w, const DevParams& d) {
-    return double(w * d.rho_ref + __bfloat162float(*p) * d.inv_scale);
+    return double(fmaf(__bfloat162float(*p), d.inv_scale, __fmul_rn(w, d.rho_ref)));
 }
 
 template <class Codec>
@@ -157,11 +177,11 @@ template <>
 __device__ __forceinline__ void encode_rt<CodecF32>(float* p, float, double v, const DevParams&) { *p = float(v); }
 template <>
 __device__ __forceinline__ void encode_rt<CodecF16Dev>(__half* p, float w, double v, const DevParams& d) {
-    *p = __float2half_rn((float(v) - w * d.rho_ref) * d.scale);
+    *p = __float2half_rn((float(v) - __fmul_rn(w, d.rho_ref)) * d.scale);
 }
 template <>
 __device__ __forceinline__ void encode_rt<CodecBF16Dev>(__nv_bfloat16* p, float w, double v, const DevParams& d) {
-    *p = __float2bfloat16_rn((float(v) - w * d.rho_ref) * d.scale);
+    *p = __float2bfloat16_rn((float(v) - __fmul_rn(w, d.rho_ref)) * d.scale);
 }
 
 }  // namespace lbm

@@ -146,7 +146,7 @@ extern "C" lbm_status lbm_diag_noalloc(const void* f, int storage, int nx, int n
     double* scratch = nullptr;
     cudaError_t e = scratch_address(&scratch);
     if (e != cudaSuccess) return LBM_ECUDA;
-    DevParams dev{float(rho_ref), float(dev_scale), float(1.0 / (dev_scale > 0 ? dev_scale : 1.0))};
+    const DevParams dev = make_dev_params(rho_ref, dev_scale > 0 ? dev_scale : 1.0);
     switch (storage) {
         case LBM_F64: e = launch_slices<CodecF64>(scratch, f, nx, ny, nz, rho_l, rho_v, dev, st); break;
         case LBM_F32: e = launch_slices<CodecF32>(scratch, f, nx, ny, nz, rho_l, rho_v, dev, st); break;

@@ -762,9 +762,7 @@ lbm_status lbm_create(const lbm_params* p, lbm_ctx** out) {
     c->coll = collision_kernel(*p, a.s);
     a.err = c->dev_err;
     a.test_stall = p->test_stall ? 1 : 0;
-    a.dev.rho_ref = float(p->rho_ref);
-    a.dev.scale = float(p->dev_scale);
-    a.dev.inv_scale = float(1.0 / p->dev_scale);
+    a.dev = make_dev_params(p->rho_ref, p->dev_scale);
     {
         char why[400] = {0};
         if (lbm_status st = configure_step(c, p->kernel, p->tile_y, p->zchunk, why, sizeof(why)); st != LBM_OK) {

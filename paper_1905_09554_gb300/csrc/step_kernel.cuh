@@ -230,12 +230,9 @@ __device__ __forceinline__ void collide_mrt(R (&f)[Q], R Fx, R Fy, R Fz, const R
 // S = F), rows with s = 1 vanish, and
 //   f* = f_eq(rho, u_b) + S_pop/2 + sum_{k in K} M_k^T (1 - s_k)(m_k - m_eq_k + S_k/2)/norm_k.
 // Algebraically identical to collide_mrt for such rates, with far fewer
-// operations (only the even rows of K are transformed).  WITH_E = false
-// leaves out the energy row (its rate is 1: the shear rule), whose
-// correction is then exactly zero.
-template <class R, bool UNIT, bool WITH_E>
-__device__ __forceinline__ void collide_mrt_sparse_rows(R (&f)[Q], R Fx, R Fy, R Fz, const R (&s)[Q]) {
-    constexpr int K0 = WITH_E ? 0 : 1;  // first row of K transformed
+// operations (only the even rows of K are transformed).
+template <class R, bool UNIT>
+__device__ __forceinline__ void collide_mrt_sparse(R (&f)[Q], R Fx, R Fy, R Fz, const R (&s)[Q]) {
     R ps[9], rho = f[0], jx = R(0), jy = R(0), jz = R(0);
     static_for<0, 9>([&](auto pc) {
         constexpr int p = decltype(pc)::value, q = 2 * p + 1;
@@ -263,7 +260,7 @@ __device__ __forceinline__ void collide_mrt_sparse_rows(R (&f)[Q], R Fx, R Fy, R
         const R meq[6] = {rho * (R(-11) + R(19) * u2), rho * pxx, rho * pww, rho * ux * uy, rho * uy * uz,
                           rho * ux * uz};
         const R sg[6] = {R(38) * uF, R(2) * gxx, R(2) * gww, ux * Fy + uy * Fx, uy * Fz + uz * Fy, ux * Fz + uz * Fx};
-        static_for<K0, 6>([&](auto ic) {
+        static_for<0, 6>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             constexpr int k = KS[i];
             R m = R(0);
@@ -283,7 +280,7 @@ __device__ __forceinline__ void collide_mrt_sparse_rows(R (&f)[Q], R Fx, R Fy, R
         constexpr int q = decltype(qc)::value;
         R acc = R(0);
         if constexpr (!UNIT) {
-            static_for<K0, 6>([&](auto ic) {
+            static_for<0, 6>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 constexpr int c = mrt_coef(KS[i], q);
                 if constexpr (c == 1) acc += dk[i];
@@ -317,13 +314,6 @@ __device__ __forceinline__ void collide_mrt_sparse_rows(R (&f)[Q], R Fx, R Fy, R
         f[q] = e + odd;
         f[q + 1] = e - odd;
     });
-}
-
-template <class R, bool UNIT>
-__device__ __forceinline__ void collide_mrt_sparse(R (&f)[Q], R Fx, R Fy, R Fz, const R (&s)[Q]) {
-    if constexpr (UNIT) collide_mrt_sparse_rows<R, true, false>(f, Fx, Fy, Fz, s);
-    else if (s[1] == R(1)) collide_mrt_sparse_rows<R, false, false>(f, Fx, Fy, Fz, s);  // the shear rule
-    else collide_mrt_sparse_rows<R, false, true>(f, Fx, Fy, Fz, s);
 }
 
 template <class Codec>

@@ -66,6 +66,14 @@ __device__ __forceinline__ S from_bits(uint32_t w) {
     memcpy(&v, &b, sizeof(b));
     return v;
 }
+// the two 16-bit halves of a word (low: the pair's first cell)
+template <class S>
+__device__ __forceinline__ void halves(uint32_t w, S& lo, S& hi) {
+    unsigned short l, h;
+    asm("mov.b32 {%0, %1}, %2;" : "=h"(l), "=h"(h) : "r"(w));
+    memcpy(&lo, &l, sizeof(l));
+    memcpy(&hi, &h, sizeof(h));
+}
 }  // namespace pair16
 
 template <class Codec, int COLL, int TY, class I>
@@ -157,7 +165,9 @@ sc_step_pair16_kernel(const typename Codec::S* __restrict__ src, typename Codec:
             R r = R(0);
             static_for<0, Q>([&](auto qc) {
                 constexpr int q = decltype(qc)::value;
-                const S v = pair16::from_bits<S>(hi ? (w[q] >> 16) : w[q]);
+                S v0, v1;
+                pair16::halves(w[q], v0, v1);
+                const S v = hi ? v1 : v0;
                 if constexpr (LOCAL) r += Codec::template decode_ref<q>(v, ref, dev);
                 else r += Codec::template decode<q>(v, dev);
             });
@@ -263,8 +273,9 @@ sc_step_pair16_kernel(const typename Codec::S* __restrict__ src, typename Codec:
                 const float rf = c ? ref.y : ref.x;
                 static_for<0, Q>([&](auto qc) {
                     constexpr int q = decltype(qc)::value;
-                    const uint32_t wq_ = w[q * L::NT];
-                    const S sv = pair16::from_bits<S>(c ? (wq_ >> 16) : wq_);
+                    S v0, v1;
+                    pair16::halves(w[q * L::NT], v0, v1);
+                    const S sv = c ? v1 : v0;
                     if constexpr (LOCAL) f[q] = Codec::template decode_ref<q>(sv, rf, dev);
                     else f[q] = Codec::template decode<q>(sv, dev);
                 });
@@ -290,7 +301,8 @@ sc_step_pair16_kernel(const typename Codec::S* __restrict__ src, typename Codec:
                     *reinterpret_cast<float2*>(a.ref_dst + (zoff[1] + my_xy)) = rnow;
                 }
             }
-            // Eq. LBE streaming: f_a(x + c_a, t + 1) = f*_a(x, t), as aligned words
+            // Eq. LBE streaming: f_a(x + c_a, t + 1) = f*_a(x, t), as aligned words; each
+            // store has its own lane condition, so the stores are predicated, not branched to
             static_for<0, Q>([&](auto qc) {
                 constexpr int q = decltype(qc)::value;
                 S* row = pop_at(dst, q, n) + (zoff[cz(q) + 1] + yoff[cy(q) + 1]);
@@ -299,19 +311,15 @@ sc_step_pair16_kernel(const typename Codec::S* __restrict__ src, typename Codec:
                 } else if constexpr (cx(q) > 0) {
                     // word (gx, gx+1) receives the left lane's second cell and this lane's first
                     const uint32_t from_left = __shfl_up_sync(0xffffffffu, e[1][q], 1);
-                    if (pair_on) {
-                        if (lane > 0) *reinterpret_cast<uint32_t*>(row + gx) = from_left | (e[0][q] << 16);
-                        else row[gx + 1] = pair16::from_bits<S>(e[0][q]);
-                        if (lane == last) row[x_right] = pair16::from_bits<S>(e[1][q]);
-                    }
+                    if (pair_on && lane > 0) *reinterpret_cast<uint32_t*>(row + gx) = from_left | (e[0][q] << 16);
+                    if (pair_on && lane == 0) row[gx + 1] = pair16::from_bits<S>(e[0][q]);
+                    if (pair_on && lane == last) row[x_right] = pair16::from_bits<S>(e[1][q]);
                 } else {
                     // word (gx, gx+1) receives this lane's second cell and the right lane's first
                     const uint32_t from_right = __shfl_down_sync(0xffffffffu, e[0][q], 1);
-                    if (pair_on) {
-                        if (lane < last) *reinterpret_cast<uint32_t*>(row + gx) = e[1][q] | (from_right << 16);
-                        else row[gx] = pair16::from_bits<S>(e[1][q]);
-                        if (lane == 0) row[x_left] = pair16::from_bits<S>(e[0][q]);
-                    }
+                    if (pair_on && lane < last) *reinterpret_cast<uint32_t*>(row + gx) = e[1][q] | (from_right << 16);
+                    if (pair_on && lane == last) row[gx] = pair16::from_bits<S>(e[1][q]);
+                    if (pair_on && lane == 0) row[x_left] = pair16::from_bits<S>(e[0][q]);
                 }
             });
         };
