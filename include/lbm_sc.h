@@ -74,7 +74,11 @@ typedef struct {
     double rho0;          /* reference density of psi (the paper fixes 1.0)        */
     int storage;          /* LBM_F64 / LBM_F32 / LBM_F16_DEV / LBM_BF16_DEV /
                              LBM_F16_LOCAL / LBM_BF16_LOCAL                          */
-    double rho_ref;       /* deviation storage: f_a = w_a rho_ref + d_a / dev_scale.
+    double rho_ref;       /* deviation storage: f_a = w_a rho_ref + d_a / dev_scale,
+                             in float arithmetic with w_a rho_ref rounded to float
+                             once per velocity (decode: fma(d_a, 1/dev_scale,
+                             w_a rho_ref); encode: (f_a - w_a rho_ref) * dev_scale
+                             rounded to nearest).
                              Local-reference storage ignores it: there rho_ref is
                              a float field R(x) the library allocates (2 x 4 bytes
                              per cell beside the populations), set from each cell's
