@@ -396,7 +396,9 @@ int collision_kernel(const lbm_params& p, const double (&s)[Q]) {
             if (!in_k) sparse = false;
         }
     }
-    return unit ? COLL_MRT_UNIT : (sparse ? COLL_MRT_SPARSE : COLL_MRT);
+    if (unit) return COLL_MRT_UNIT;
+    if (!sparse) return COLL_MRT;
+    return s[1] == 1.0 ? COLL_MRT_SHEAR : COLL_MRT_SPARSE;  // e at 1: the shear rule
 }
 
 // Run `fn.template operator()<Codec>()` for the context's storage type.

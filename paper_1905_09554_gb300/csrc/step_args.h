@@ -11,8 +11,9 @@
 namespace lbm {
 
 // Collision kernels: SRT; MRT with general rates; MRT whose rates outside
-// {e, 3pxx, pww, pxy, pyz, pxz} are 1; MRT with every rate 1.
-enum { COLL_SRT = 0, COLL_MRT = 1, COLL_MRT_SPARSE = 2, COLL_MRT_UNIT = 3, COLL_COUNT = 4 };
+// {e, 3pxx, pww, pxy, pyz, pxz} are 1; MRT with every rate 1; MRT whose
+// rates outside {3pxx, pww, pxy, pyz, pxz} are 1 (the shear rule).
+enum { COLL_SRT = 0, COLL_MRT = 1, COLL_MRT_SPARSE = 2, COLL_MRT_UNIT = 3, COLL_MRT_SHEAR = 4, COLL_COUNT = 5 };
 
 struct StepArgs {
     int nx, ny, nz;
@@ -81,7 +82,7 @@ struct StepLaunch {
     const CUtensorMap* tmap;  // kernel 5: tensor map of the source copy
     int tile_y;           // 4, 8 or 16 (tile width is 32)
     int grid;             // persistent grid (kernels 2 and 3)
-    int coll;             // COLL_SRT .. COLL_MRT_UNIT
+    int coll;             // COLL_SRT .. COLL_MRT_SHEAR
     cudaStream_t stream;
 };
 
@@ -97,7 +98,7 @@ struct StepKernels {
     int (*batch_prepare)(const StepLaunch& l);
 };
 
-// storage: LBM_F64 .. LBM_BF16_LOCAL (0..5); coll: COLL_SRT .. COLL_MRT_UNIT.
+// storage: LBM_F64 .. LBM_BF16_LOCAL (0..5); coll: COLL_SRT .. COLL_MRT_SHEAR.
 const StepKernels& step_kernels(int storage, int coll);
 
 }  // namespace lbm

@@ -230,9 +230,13 @@ __device__ __forceinline__ void collide_mrt(R (&f)[Q], R Fx, R Fy, R Fz, const R
 // S = F), rows with s = 1 vanish, and
 //   f* = f_eq(rho, u_b) + S_pop/2 + sum_{k in K} M_k^T (1 - s_k)(m_k - m_eq_k + S_k/2)/norm_k.
 // Algebraically identical to collide_mrt for such rates, with far fewer
-// operations (only the even rows of K are transformed).
-template <class R, bool UNIT>
+// operations (only the even rows of K are transformed).  WITH_E = false is
+// the shear rule's form: the energy row relaxes at 1 there, its correction
+// is exactly zero and the row is left out (a separate instantiation, chosen
+// on the host, so no kernel carries both forms).
+template <class R, bool UNIT, bool WITH_E = true>
 __device__ __forceinline__ void collide_mrt_sparse(R (&f)[Q], R Fx, R Fy, R Fz, const R (&s)[Q]) {
+    constexpr int K0 = WITH_E ? 0 : 1;  // first row of K transformed
     R ps[9], rho = f[0], jx = R(0), jy = R(0), jz = R(0);
     static_for<0, 9>([&](auto pc) {
         constexpr int p = decltype(pc)::value, q = 2 * p + 1;
@@ -260,7 +264,7 @@ __device__ __forceinline__ void collide_mrt_sparse(R (&f)[Q], R Fx, R Fy, R Fz, 
         const R meq[6] = {rho * (R(-11) + R(19) * u2), rho * pxx, rho * pww, rho * ux * uy, rho * uy * uz,
                           rho * ux * uz};
         const R sg[6] = {R(38) * uF, R(2) * gxx, R(2) * gww, ux * Fy + uy * Fx, uy * Fz + uz * Fy, ux * Fz + uz * Fx};
-        static_for<0, 6>([&](auto ic) {
+        static_for<K0, 6>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             constexpr int k = KS[i];
             R m = R(0);
@@ -280,7 +284,7 @@ __device__ __forceinline__ void collide_mrt_sparse(R (&f)[Q], R Fx, R Fy, R Fz, 
         constexpr int q = decltype(qc)::value;
         R acc = R(0);
         if constexpr (!UNIT) {
-            static_for<0, 6>([&](auto ic) {
+            static_for<K0, 6>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 constexpr int c = mrt_coef(KS[i], q);
                 if constexpr (c == 1) acc += dk[i];
@@ -355,6 +359,7 @@ __device__ __forceinline__ void update_cell(typename Codec::R (&fc)[Q], const ty
     if constexpr (COLL == COLL_SRT) collide_srt<R>(fc, Fx, Fy, Fz, par<R>(a.tau, a.tauf), par<R>(a.omega, a.omegaf));
     else if constexpr (COLL == COLL_MRT) collide_mrt<R>(fc, Fx, Fy, Fz, rates<R>(a));
     else if constexpr (COLL == COLL_MRT_SPARSE) collide_mrt_sparse<R, false>(fc, Fx, Fy, Fz, rates<R>(a));
+    else if constexpr (COLL == COLL_MRT_SHEAR) collide_mrt_sparse<R, false, false>(fc, Fx, Fy, Fz, rates<R>(a));
     else collide_mrt_sparse<R, true>(fc, Fx, Fy, Fz, rates<R>(a));
 
     // Eq. LBE streaming: f_a(x + c_a, t + 1) = f*_a(x, t).

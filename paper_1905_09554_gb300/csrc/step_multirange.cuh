@@ -101,6 +101,8 @@ sc_step_mr_kernel(const typename Codec::S* __restrict__ src, typename Codec::S* 
                 collide_srt<R>(fc, Fx, Fy, Fz, par<R>(a.tau, a.tauf), par<R>(a.omega, a.omegaf));
             else if constexpr (COLL == COLL_MRT) collide_mrt<R>(fc, Fx, Fy, Fz, rates<R>(a));
             else if constexpr (COLL == COLL_MRT_SPARSE) collide_mrt_sparse<R, false>(fc, Fx, Fy, Fz, rates<R>(a));
+            else if constexpr (COLL == COLL_MRT_SHEAR)
+                collide_mrt_sparse<R, false, false>(fc, Fx, Fy, Fz, rates<R>(a));
             else collide_mrt_sparse<R, true>(fc, Fx, Fy, Fz, rates<R>(a));
             // Eq. LBE streaming: f_a(x + c_a, t + 1) = f*_a(x, t).
             const int zm = (z == 0) ? nz - 1 : z - 1, zn = (z + 1 == nz) ? 0 : z + 1;

@@ -283,6 +283,8 @@ sc_step_pair16_kernel(const typename Codec::S* __restrict__ src, typename Codec:
                 else if constexpr (COLL == COLL_MRT) collide_mrt<R>(f, F[c][0], F[c][1], F[c][2], a.sf);
                 else if constexpr (COLL == COLL_MRT_SPARSE)
                     collide_mrt_sparse<R, false>(f, F[c][0], F[c][1], F[c][2], a.sf);
+                else if constexpr (COLL == COLL_MRT_SHEAR)
+                    collide_mrt_sparse<R, false, false>(f, F[c][0], F[c][1], F[c][2], a.sf);
                 else collide_mrt_sparse<R, true>(f, F[c][0], F[c][1], F[c][2], a.sf);
                 static_for<0, Q>([&](auto qc) {
                     constexpr int q = decltype(qc)::value;
