@@ -442,6 +442,24 @@ lbm_status check_device_error(lbm_ctx* c) {
     return LBM_OK;
 }
 
+// Planes (plus one per work item for the two halo planes it reads first)
+// on the busiest block when `grid` persistent blocks take the work items
+// (tile, chunk of z planes), numbered chunk-major, round-robin.
+long long busiest_block_planes(long long nz, long long tiles, long long grid, long long zc) {
+    if (grid < 1 || tiles < 1 || zc < 1) return 0;
+    const long long chunks = (nz + zc - 1) / zc, last = nz - (chunks - 1) * zc;
+    const long long items = tiles * chunks;
+    std::vector<long long> in_last(grid, 0);  // items of the last (shorter) chunk per block
+    for (long long i = (chunks - 1) * tiles; i < items; ++i) ++in_last[i % grid];
+    long long worst = 0;
+    for (long long b = 0; b < grid; ++b) {
+        const long long n = items / grid + (b < items % grid ? 1 : 0);
+        const long long load = n * (zc + 1) - (zc - last) * in_last[b];
+        if (load > worst) worst = load;
+    }
+    return worst;
+}
+
 int auto_zchunk(const lbm_ctx* c) {
     const long long xy_blocks = (long long)((c->p.nx + 31) / 32) * ((c->p.ny + c->tile_y - 1) / c->tile_y);
     // Aim at ~4 blocks per SM in total so that the tail of the grid is short,
@@ -552,30 +570,36 @@ lbm_status configure_step(lbm_ctx* c, int kernel, int tile_y, int zchunk, char* 
     if (zchunk) {
         c->zchunk = zchunk < p->nz ? zchunk : p->nz;
     } else if (c->kernel >= 2 && c->kernel != 6) {
-        // At least about 8 work items per block of the persistent grid, and
-        // short chunks: the address range that all blocks touch at once grows
-        // with the chunk length times the plane size.  Measured on GB300, SRT
+        // The longest chunk first: the address range that all blocks touch
+        // at once grows with the chunk length times the plane size, so at
+        // most 24 MiB of one population's planes (16..96 planes), and 8
+        // planes for planes of 1.5 MiB and more.  Measured on GB300, FP32 SRT
         // on 32x16 tiles (GLUPS for chunks of 16 / 32 / 64 planes):
-        // 256^2 x 575 31.8 / 32.0 / 31.9, 576^2 x 1536 30.1 / 29.8 / 28.4,
-        // 640^2 x 1437 30.3 / 26.6 / 25.2, 672^2 x 1792 28.7 / 22.9 / 21.7;
-        // 512^2 x 1149 with 383-plane chunks 25.8.  So at most 32 planes, and
-        // for 32x16 tiles at most 24 MiB of one population's planes (>= 16);
-        // the 32x4 MRT tiles measured best at 32 on the large boxes.
+        // 576^2 x 1536 30.1 / 29.8 / 28.4, 640^2 x 1437 30.3 / 26.6 / 25.2,
+        // 672^2 x 1792 28.7 / 22.9 / 21.7 (6 / 8 / 12 planes: 27.7 / 28.7 /
+        // 20.0).
+        const long long plane_bytes = (long long)p->nx * p->ny * (long long)c->elem;
+        long long zmax = (24LL << 20) / (plane_bytes > 0 ? plane_bytes : 1);
+        zmax = zmax < 16 ? 16 : (zmax > 96 ? 96 : zmax);
+        if (c->tile_y >= 16 && plane_bytes >= (3LL << 19)) zmax = 8;
+        if (zmax > p->nz) zmax = p->nz;
+        // Within that bound, the chunk that spreads the planes most evenly
+        // over the persistent blocks, which take the work items round-robin:
+        // the least planes on the busiest block (busiest_block_planes).  On
+        // 256^2 x 575 (128 tiles of 32x16, 152 blocks) chunks of 32 / 44 / 72
+        // planes put 527 / 499 / 510 planes on the busiest block and ran at
+        // 32.15 / 33.87 / 33.47 GLUPS (MRT at tau = 0.8: 30.72 / 32.42 /
+        // 31.84).
         const long long tiles = (long long)tiles_x * tiles_y;
-        long long chunks = (8LL * c->grid + tiles - 1) / tiles;
-        long long zc = (p->nz + chunks - 1) / chunks;
-        long long zmax = 32;
-        if (c->tile_y >= 16) {
-            const long long plane_bytes = (long long)p->nx * p->ny * (long long)c->elem;
-            zmax = (24LL << 20) / (plane_bytes > 0 ? plane_bytes : 1);
-            zmax = zmax < 16 ? 16 : (zmax > 32 ? 32 : zmax);
-            // planes of a population of 1.5 MiB and more (672^2 FP32, the
-            // paper's R0 = 98 box): 8 planes, measured 28.7 GLUPS against
-            // 27.7 / 20.0 / 25.0 for 6 / 12 / 16
-            if (plane_bytes >= (3LL << 19)) zmax = 8;
+        const long long zlo = zmax < 8 ? zmax : 8;
+        long long zc = zmax, best = -1;
+        for (long long z = zmax; z >= zlo; --z) {  // ties: the longer chunk
+            const long long load = busiest_block_planes(p->nz, tiles, c->grid, z);
+            if (best < 0 || load < best) {
+                best = load;
+                zc = z;
+            }
         }
-        if (zc > zmax) zc = zmax;
-        if (zc < 8) zc = 8;
         c->zchunk = int(zc < p->nz ? zc : p->nz);
     } else {
         c->zchunk = auto_zchunk(c);
