@@ -347,7 +347,7 @@ lbm_status lbm_batch_box(lbm_batch *b, int i, lbm_ctx **view);
 lbm_status lbm_batch_step(lbm_batch *b, long n);
 
 /* Autotune the launch shape: times trial_steps steps for each tile height in
- * {4, 8, 16} and z chunk in {8, 16, 32, 64}, keeps the fastest and reports it
+ * {4, 8, 16} and z chunk in {8, 16, 24, 32, 48, 64}, keeps the fastest and reports it
  * (any pointer may be NULL).  The trial steps overwrite the populations:
  * tune first, then initialise the boxes. */
 lbm_status lbm_batch_tune(lbm_batch *b, int trial_steps, int *tile_y,

@@ -1443,7 +1443,7 @@ lbm_status lbm_batch_tune(lbm_batch* b, int trial_steps, int* tile_y, int* zchun
     if (!b) return LBM_EINVAL;
     if (trial_steps < 1) return b->fail(LBM_EINVAL, "lbm_batch_tune: trial_steps must be >= 1");
     const int tys[3] = {4, 8, 16};
-    const int zcs[4] = {8, 16, 32, 64};
+    const int zcs[6] = {8, 16, 24, 32, 48, 64};
     cudaEvent_t e0, e1;
     LBM_CUDA(b, cudaEventCreate(&e0));
     LBM_CUDA(b, cudaEventCreate(&e1));

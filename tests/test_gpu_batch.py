@@ -63,7 +63,7 @@ def test_batch_box_matches_the_reference():
 def test_autotune_then_run_is_still_exact():
     with lbm.Batch(DIMS, G=G, tau=1.0, storage="f32") as B:
         best = B.tune(trial_steps=2)
-        assert best["tile_y"] in (4, 8, 16) and best["zchunk"] in (8, 16, 32, 64)
+        assert best["tile_y"] in (4, 8, 16) and best["zchunk"] in (8, 16, 24, 32, 48, 64)
         assert best["ms_per_step"] > 0
         cfg = B.config()
         assert (cfg["tile_y"], cfg["zchunk"]) == (best["tile_y"], best["zchunk"])
